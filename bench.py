@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: single-source 2-RPQ queries/s on one GB300 (or N replicas).
+
+Workload (default ``rmat20``): R-MAT scale 20 (1,048,576 vertices, 2^24 edge
+samples, a=0.57 b=c=0.19), 8 labels with Zipf(1.0) frequencies, seed 1; 400
+queries = templates a*, a.b*, (a|b)*.c, a^-.b* x 100 random sources with
+non-zero degree; queries run one at a time, as in the paper's evaluation
+(section 5.3: data preloaded, sequential isolated queries).
+
+One step = those 400 queries.  ``value`` = queries/s with the graph and the
+outputs resident on the device (rpq_query with a device output buffer,
+CUDA events on the launching stream around each step, L2 flushed between
+steps).  ``e2e`` = the same queries through the public API with host
+output buffers and regex compilation inside the timed region.  The roofline
+line refers to the traversal kernel (one cooperative launch per query).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+PROFILE_JSON = os.path.join(ROOT, "profiles", "rpq_query_kernel_rmat20.json")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2412_10287_gb300", "csrc", "query.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--per-template", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="CPU work budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def sha256(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def profile_traffic():
+    """Per-launch DRAM bytes of the traversal kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    try:
+        with open(PROFILE_JSON) as f:
+            pj = json.load(f)
+        if pj.get("kernel_source_sha256") != sha256(KERNEL_SOURCE):
+            return None
+        return pj.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.remove(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def workload(per_template):
+    from paper_2412_10287_gb300 import workloads as W
+
+    return W.config2(per_template=per_template)
+
+
+def workload_config(w, n_queries, extra=None):
+    c = {"workload": "rmat20: R-MAT scale 20 (1,048,576 vertices, 2^24 edge samples, "
+                     "a=0.57 b=c=0.19), 8 labels Zipf(1.0), seed 1; "
+                     f"{n_queries} single-source queries (a*, a.b*, (a|b)*.c, a^-.b*), "
+                     "one at a time",
+         "n_vertices": w.graph.n, "n_edge_samples": w.graph.m, "n_labels": w.graph.n_labels,
+         "queries_per_step": n_queries,
+         "l2": "flushed between steps (256 MiB write)",
+         "parallelism": "replicas (query-sharded, no collective)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------- CPU oracle ----
+
+def oracle_sample(w, seconds_budget, max_threads=None):
+    """Times the CPU oracle (as it stands) on a stratified sample of the
+    workload's queries, on the host cores (one query per thread)."""
+    from oracle import oracle as O
+    from oracle.regex_nfa import compile_regex
+
+    g = w.graph
+    og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+    threads = max_threads or len(os.sched_getaffinity(0))
+    qs = w.queries
+    # estimate the per-query cost on a small probe, then size the sample
+    probe = [qs[i] for i in range(0, len(qs), max(1, len(qs) // 8))][:8]
+    t0 = time.perf_counter()
+    for q in probe:
+        og.ssr(compile_regex(q.regex, g.n_labels), q.source)
+    per_q = (time.perf_counter() - t0) / max(1, len(probe))
+    n_sample = int(max(threads, min(len(qs), seconds_budget / max(per_q, 1e-6))))
+    stride = max(1, len(qs) // n_sample)
+    sample = qs[::stride][:n_sample]
+    nfas = [compile_regex(q.regex, g.n_labels) for q in sample]
+
+    def run(i):
+        return og.ssr(nfas[i], sample[i].source)["counters"]["answer"]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(run, range(len(sample))))
+    wall = time.perf_counter() - t0
+    og.close()
+    return {"value": len(sample) / wall, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(qs)} queries (every {stride}th), "
+                      f"{threads} threads, one query per thread; adjacency lists built before "
+                      f"timing; {wall:.1f} s wall"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    w = workload(args.per_template)
+    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(w, per_step_budget * 4)
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.median([r["value"] for r in vals])
+    line = {"impl": "reference", "metric": "rpq_queries_per_s", "value": v, "unit": "queries/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * len(w.queries) / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(w, len(w.queries),
+                                      {"note": "CPU oracle timed on a bounded sample per step"}),
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": vals[-1]["cores"],
+                             "kind": "oracle", "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU path ---
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2412_10287_gb300 import rpq as R
+
+    w = workload(args.per_template)
+    g = w.graph
+    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
+    srcs = [q.source for q in w.queries]
+    nq = len(srcs)
+    stream = torch.cuda.current_stream()
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    W_words = (g.n + 63) // 64
+
+    def one_step(collect):
+        res = []
+        for nfa, s in zip(nfas, srcs):
+            t0 = time.perf_counter()
+            cnt, st = R.rpq_query(gg, nfa, s, out=out, stream=stream, with_stats=True)
+            if collect:
+                res.append((time.perf_counter() - t0, st, nfa.info()[0]))
+        return res
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+
+    step_ms, recs = [], []
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            if ws > 1:
+                torch.distributed.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            recs.extend(one_step(True))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    clocks = clk.summary()
+    total_s = sum(step_ms) / 1000.0
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws * nq * args.steps / total_s
+
+    lat = sorted(r[0] * 1000.0 for r in recs)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+    kern_ms = [r[1]["device_ms"] for r in recs]
+    push_bytes = sum(r[1]["push_bytes"] for r in recs)
+    sweep_bytes = sum(3 * r[2] * W_words * 8 * (r[1]["levels"] + 1) for r in recs)
+    prod_edges = sum(r[1]["product_edges"] for r in recs)
+    alg_bytes_per_launch = (push_bytes + sweep_bytes) / len(recs)
+    avg_launch_s = sum(kern_ms) / len(kern_ms) / 1000.0
+    achieved = alg_bytes_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = measured_peak()
+
+    # end to end through the public API: compile + query with host outputs
+    e2e_steps, h2d, d2h = [], 0, 0
+    for k in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in w.queries:
+            nfa = R.rpq_nfa_compile(q.regex, g.n_labels)
+            ans, st = R.rpq_query(gg, nfa, q.source, stream=stream, with_stats=True)
+            if k == 0:
+                h2d += st["h2d_bytes"]
+                d2h += st["d2h_bytes"]
+        e2e_steps.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_steps)
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * nq * args.steps / e2e_s
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "rpq_queries_per_s", "value": value, "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(w, nq),
+            "p50_ms": p50, "p99_ms": p99,
+            "product_edges_per_s": ws * prod_edges / (total_s if ws == 1 else total_s),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profile_traffic(),
+                         "kernel": "rpq_query_kernel",
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "algorithmic_bytes_per_launch": alg_bytes_per_launch,
+                         "avg_launch_ms": avg_launch_s * 1000.0},
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": nq * args.steps,
+            "clocks": clocks,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

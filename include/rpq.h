@@ -1,0 +1,250 @@
+/*
+ * rpq.h -- C ABI of the GB300 single-source 2-RPQ library (librpq.so).
+ *
+ * Implements the method of "Single-Source Regular Path Querying in Terms of
+ * Linear Algebra" (arXiv:2412.10287): a level-synchronous breadth-first
+ * search over the product of an edge-labelled graph and a query automaton
+ * (section 4, Algorithm 1).  Every level computes
+ *     M <- ( OR_a (N^a)^T x M x G^a ) <not P>,   P <- P + M,
+ * until M = 0, and the answer is F x P.  The traversal runs in hand-written
+ * CUDA kernels for sm_103a; the host code only validates, builds the
+ * automaton and moves data.
+ *
+ * Conventions for every call:
+ *   - Every call returns an rpq_status; nothing throws across the ABI.
+ *     rpq_last_error() gives a message for the last failure on this thread.
+ *   - Vertex ids are 0-based int32 in [0, n) (the paper numbers them 1..|V|,
+ *     section 2).  Label ids are int32 in [0, L); in automaton transitions a
+ *     label a in [L, 2L) denotes the inverse label (a-L)^- of section 2.
+ *   - Inputs are copied: the caller keeps ownership of every array it passes.
+ *     Handles (rpq_graph, rpq_nfa, rpq_server) are owned by the library and
+ *     released with the matching *_free / *_destroy call.  Output arrays are
+ *     owned by the caller.
+ *   - Output arrays may be host or device memory (detected per call).  When a
+ *     result does not fit in `capacity`, the call returns RPQ_ERR_CAPACITY and
+ *     sets the count to the full size, so the caller can retry with a larger
+ *     buffer.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that return results synchronise that stream before returning.
+ *   - Graphs and automata are immutable once created and may be shared
+ *     between threads.  Queries on one graph from several threads are safe;
+ *     each takes its own device workspace.
+ */
+#ifndef RPQ_H
+#define RPQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rpq_status {
+    RPQ_OK = 0,
+    RPQ_ERR_INVALID = 1,  /* bad argument: id out of range, null pointer, > 64 states ... */
+    RPQ_ERR_PARSE = 2,    /* regular expression syntax error */
+    RPQ_ERR_OOM = 3,      /* device or host allocation failed */
+    RPQ_ERR_CUDA = 4,     /* a CUDA call failed (message in rpq_last_error) */
+    RPQ_ERR_TIMEOUT = 5,  /* a device-side wait exceeded its limit; the query was abandoned */
+    RPQ_ERR_CAPACITY = 6, /* output buffer too small; the count holds the size needed */
+    RPQ_ERR_BUSY = 7      /* server queue full / result not ready yet */
+} rpq_status;
+
+typedef struct rpq_graph rpq_graph;
+typedef struct rpq_nfa rpq_nfa;
+typedef struct rpq_server rpq_server;
+
+/* Per-query counters.  The first six fields are properties of
+ * (graph, automaton, source, max_levels) alone, identical for any correct
+ * implementation of Algorithm 1. */
+typedef struct rpq_stats {
+    int64_t levels;          /* non-empty levels after level 0 (BFS depth) */
+    int64_t visited_pairs;   /* |P|: (state, vertex) pairs reached */
+    int64_t expanded_pairs;  /* pairs whose out-edges were traversed */
+    int64_t product_edges;   /* sum over expanded (q,v) of |delta(q,a)| * deg_a(v) */
+    int64_t push_bytes;      /* sum over expanded (q,v), labels a with delta(q,a) != {}: 8 + 4 deg_a(v) */
+    int64_t answer_count;    /* |answer| */
+    int64_t push_unit_levels;/* (level, unit) steps run as push (implementation detail) */
+    int64_t pull_unit_levels;/* (level, unit) steps run as pull (implementation detail) */
+    int64_t h2d_bytes;       /* bytes this call copied host -> device */
+    int64_t d2h_bytes;       /* bytes this call copied device -> host */
+    double device_ms;        /* device time of the traversal kernel, or -1 if not timed */
+} rpq_stats;
+
+/* ------------------------------------------------------------- memory -- */
+
+/* Replace the device allocator used for graphs and workspaces (for example
+ * with PyTorch's caching allocator).  alloc(size, ctx) returns device memory
+ * or NULL; free(ptr, ctx) releases it.  Pass NULLs to restore cudaMalloc /
+ * cudaFree.  Must be called while no graph or server exists. */
+rpq_status rpq_set_allocator(void *(*alloc)(size_t size, void *ctx),
+                             void (*free_fn)(void *ptr, void *ctx), void *ctx);
+
+/* --------------------------------------------------------------- graph -- */
+
+/* Builds the per-label Boolean decomposition {G^a} of section 3 on the
+ * device: for each label a, a CSR (out-edges, G^a) and a CSC (in-edges,
+ * (G^a)^T = G^{a^-}) with int32 ids, rows sorted, duplicate (u, v, a) triples
+ * removed (the matrices are Boolean).  Both forms stay resident, as in the
+ * paper's implementation (section 5).  Labels with few non-empty rows are
+ * stored hypersparse (sorted row ids + offsets).
+ *   src, dst, label: host arrays of n_edges entries; edge src[i] -label[i]-> dst[i].
+ *   Errors: RPQ_ERR_INVALID if an id is out of range or a label holds 2^31 or
+ *   more distinct edges; RPQ_ERR_OOM; RPQ_ERR_CUDA. */
+rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64_t n_edges,
+                          const int32_t *src, const int32_t *dst, const int32_t *label,
+                          void *stream, rpq_graph **out);
+void rpq_graph_free(rpq_graph *g);
+
+/* Sizes of a loaded graph: distinct edges of label `label` (or of all labels
+ * when label < 0). */
+rpq_status rpq_graph_info(const rpq_graph *g, int32_t label, int32_t *n_vertices,
+                          int32_t *n_labels, int64_t *n_edges);
+
+/* Copies the CSR (inverse = 0) or CSC (inverse = 1) of one label to host
+ * arrays in dense form: offsets[n+1] (int64) and neighbours[nnz] (int32).
+ * Pass neighbours = NULL to get the offsets only. */
+rpq_status rpq_graph_export(const rpq_graph *g, int32_t label, int32_t inverse,
+                            int64_t *offsets, int32_t *neighbours, int64_t capacity);
+
+/* ---------------------------------------------------------- automaton -- */
+
+/* Compiles a regular expression over labels and inverse labels into a
+ * minimised DFA (section 5.2: queries become minimised DFAs), dead state
+ * dropped.  Syntax:
+ *     alt  := seq ('|' seq)*
+ *     seq  := post (['/' | '.' | U+00B7 | whitespace] post)*   (juxtaposition concatenates)
+ *     post := atom ('*' | '+' | '?')*
+ *     atom := LABEL | '^' atom | '(' alt ')'
+ * LABEL is a decimal id in [0, n_labels); '^R' is the inverse language R^-
+ * (words reversed, every label inverted; section 4).
+ *   Errors: RPQ_ERR_PARSE (syntax), RPQ_ERR_INVALID (label out of range, or
+ *   more than 64 states after minimisation). */
+rpq_status rpq_nfa_compile(const char *regex, int32_t n_labels, rpq_nfa **out);
+
+/* Uses a given automaton verbatim (section 2, 2-NFA): n_states <= 64,
+ * transitions from[i] -label[i]-> to[i] with label in [0, 2 n_labels), start
+ * and final state lists.  Several start states and non-determinism are
+ * allowed. */
+rpq_status rpq_nfa_from_transitions(int32_t n_states, int32_t n_labels, int32_t n_trans,
+                                    const int32_t *from, const int32_t *to,
+                                    const int32_t *label, int32_t n_start,
+                                    const int32_t *starts, int32_t n_final,
+                                    const int32_t *finals, rpq_nfa **out);
+void rpq_nfa_free(rpq_nfa *nfa);
+
+/* Number of states and transitions of an automaton. */
+rpq_status rpq_nfa_info(const rpq_nfa *nfa, int32_t *n_states, int32_t *n_trans,
+                        int32_t *n_labels);
+
+/* Copies the transitions (capacity entries each) and the start/final masks
+ * (bit q set = state q) of an automaton to host memory. */
+rpq_status rpq_nfa_export(const rpq_nfa *nfa, int32_t *from, int32_t *to, int32_t *label,
+                          int32_t capacity, uint64_t *start_mask, uint64_t *final_mask);
+
+/* Whether the automaton accepts a word of symbols in [0, 2L) (host-side
+ * simulation; for checking compiled automata). */
+rpq_status rpq_nfa_accepts(const rpq_nfa *nfa, const int32_t *word, int32_t length,
+                           int32_t *accepted);
+
+/* Reversed automaton N^- of section 4 (transitions reversed with inverted
+ * labels, start and final sets swapped): SSR with N^- from v answers the
+ * single-destination query of N for v. */
+rpq_status rpq_nfa_reverse(const rpq_nfa *nfa, rpq_nfa **out);
+
+/* -------------------------------------------------------------- query -- */
+
+/* Single-source 2-RPQ (section 2, single-source reachability): the vertices v
+ * such that some 2-path from `source` to v spells a word accepted by `nfa`,
+ * in ascending order.  Runs Algorithm 1 on the device in one persistent
+ * kernel; each level expands the frontier by push (sparse frontier) or pull
+ * (dense frontier) per (label, target state).
+ *   max_levels: 0 = until the frontier is empty; k > 0 = pairs reached by
+ *     words of length <= k only (P_k of section 4).
+ *   out_vertices/capacity/out_count: the answer (see conventions).
+ *   stats: may be NULL.
+ *   Errors: RPQ_ERR_INVALID (source outside [0,n), labels of nfa beyond the
+ *   graph's), RPQ_ERR_CAPACITY, RPQ_ERR_TIMEOUT, RPQ_ERR_CUDA, RPQ_ERR_OOM. */
+rpq_status rpq_query(const rpq_graph *g, const rpq_nfa *nfa, int32_t source, int32_t max_levels,
+                     int32_t *out_vertices, int64_t capacity, int64_t *out_count,
+                     rpq_stats *stats, void *stream);
+
+/* Same query; the answer is written as a bitset of ceil(n/64) uint64 words
+ * (bit v of word v/64 set iff v answers).  `out_bits` host or device. */
+rpq_status rpq_query_bitset(const rpq_graph *g, const rpq_nfa *nfa, int32_t source,
+                            int32_t max_levels, uint64_t *out_bits, int64_t *out_count,
+                            rpq_stats *stats, void *stream);
+
+/* Many single-source queries in one launch: query i is (nfas[i], sources[i]).
+ * Queries are packed as bit lanes of uint64 words (64 queries per lane word),
+ * so one pass over G^a per level serves all of them (multi-source BFS,
+ * section 6).  Results are concatenated: query i's vertices (ascending) are
+ * out_vertices[out_offsets[i] .. out_offsets[i+1]).  out_offsets (n+1 int64)
+ * is always filled; RPQ_ERR_CAPACITY when the total exceeds `capacity`.
+ * `stats` may be NULL or an array of n entries.  Automata may have up to 64
+ * states each. */
+rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
+                           const int32_t *sources, int32_t max_levels, int64_t *out_offsets,
+                           int32_t *out_vertices, int64_t capacity, rpq_stats *stats,
+                           void *stream);
+
+/* ------------------------------------------------------------- serving -- */
+
+typedef struct rpq_serve_config {
+    int32_t max_lanes;       /* queries in flight on the device (multiple of 64; 0 = 256) */
+    int32_t max_states;      /* state slots per lane (0 = 16) */
+    int32_t queue_capacity;  /* submitted-but-not-admitted queries (0 = 65536) */
+    int64_t memory_budget;   /* bytes of device state the server may hold (0 = no limit) */
+    int32_t max_levels;      /* per-query level cap (0 = none) */
+    int32_t reserved;
+} rpq_serve_config;
+
+typedef struct rpq_serve_stats {
+    int64_t submitted, admitted, completed, rejected;
+    int64_t level_steps;     /* device level steps run */
+    double p50_ms, p99_ms;   /* submit -> completion latency over completed queries */
+    double mean_ms;
+    double elapsed_s;        /* since the first submission */
+    double qps;              /* completed / elapsed_s */
+} rpq_serve_stats;
+
+/* A server keeps the graph and every admitted query's state on the device
+ * and runs a host thread that (1) admits queued queries into free lanes while
+ * device memory allows, (2) advances every active lane by one level per step
+ * (a captured CUDA graph replay), (3) retires lanes whose frontier emptied and
+ * stores their answers.  Queries arriving while others run join at the next
+ * level step (continuous batching); each answer is the same as the query
+ * alone would give. */
+rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_config *cfg, rpq_server **out);
+
+/* Non-blocking.  RPQ_ERR_BUSY when the queue is full.  The automaton must
+ * stay alive until the ticket is polled complete. */
+rpq_status rpq_serve_submit(rpq_server *s, const rpq_nfa *nfa, int32_t source, uint64_t *ticket);
+
+/* RPQ_OK with the answer when done (the ticket is then released);
+ * RPQ_ERR_BUSY while running; RPQ_ERR_CAPACITY with *out_count set (the
+ * ticket is kept); RPQ_ERR_INVALID for an unknown ticket. */
+rpq_status rpq_serve_poll(rpq_server *s, uint64_t ticket, int32_t *out_vertices,
+                          int64_t capacity, int64_t *out_count);
+
+/* Blocks until every submitted query has completed (or timeout_ms passes;
+ * then RPQ_ERR_TIMEOUT). */
+rpq_status rpq_serve_drain(rpq_server *s, int64_t timeout_ms);
+
+rpq_status rpq_serve_stats_get(rpq_server *s, rpq_serve_stats *out);
+void rpq_serve_destroy(rpq_server *s);
+
+/* ---------------------------------------------------------------- misc -- */
+
+/* Message for the last failed call on the calling thread ("" if none). */
+const char *rpq_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char *rpq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPQ_H */

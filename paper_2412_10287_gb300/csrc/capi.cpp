@@ -1,0 +1,239 @@
+// C ABI entry points of librpq.so (declared in include/rpq.h): argument
+// checks, error reporting, the pluggable allocator, automaton handles and
+// the host/device output routing around the query kernels.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "rpq_internal.h"
+
+namespace rpq {
+
+namespace {
+thread_local std::string t_error;
+
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+Allocator g_alloc;
+std::atomic<int64_t> g_live_objects{0};
+}  // namespace
+
+rpq_status fail(rpq_status st, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_error = buf;
+    return st;
+}
+
+void clear_error() { t_error.clear(); }
+
+void *dev_alloc(size_t bytes) {
+    if (g_alloc.alloc) return g_alloc.alloc(bytes, g_alloc.ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    if (g_alloc.free_fn) g_alloc.free_fn(p, g_alloc.ctx);
+    else cudaFree(p);
+}
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+void count_object(int delta) { g_live_objects += delta; }
+
+}  // namespace rpq
+
+using namespace rpq;
+
+extern "C" const char *rpq_last_error(void) { return t_error.c_str(); }
+
+extern "C" const char *rpq_version(void) { return "0.1.0"; }
+
+extern "C" rpq_status rpq_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *),
+                                        void *ctx) {
+    clear_error();
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(RPQ_ERR_INVALID, "alloc and free must both be set or both be null");
+    g_alloc.alloc = alloc;
+    g_alloc.free_fn = free_fn;
+    g_alloc.ctx = ctx;
+    return RPQ_OK;
+}
+
+// ------------------------------------------------------------ automata --
+
+extern "C" rpq_status rpq_nfa_compile(const char *regex, int32_t n_labels, rpq_nfa **out) {
+    clear_error();
+    if (!out) return fail(RPQ_ERR_INVALID, "out is null");
+    *out = nullptr;
+    std::unique_ptr<rpq_nfa> h(new rpq_nfa());
+    rpq_status s = compile_regex(regex, n_labels, &h->a);
+    if (s != RPQ_OK) return s;
+    *out = h.release();
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_nfa_from_transitions(int32_t n_states, int32_t n_labels, int32_t n_trans,
+                                               const int32_t *from, const int32_t *to,
+                                               const int32_t *label, int32_t n_start,
+                                               const int32_t *starts, int32_t n_final,
+                                               const int32_t *finals, rpq_nfa **out) {
+    clear_error();
+    if (!out) return fail(RPQ_ERR_INVALID, "out is null");
+    *out = nullptr;
+    if (n_states <= 0 || n_states > kMaxStates)
+        return fail(RPQ_ERR_INVALID, "n_states must be in [1, %d]", kMaxStates);
+    if (n_labels <= 0) return fail(RPQ_ERR_INVALID, "n_labels must be positive");
+    if (n_trans < 0 || n_start < 0 || n_final < 0) return fail(RPQ_ERR_INVALID, "negative count");
+    if ((n_trans && (!from || !to || !label)) || (n_start && !starts) || (n_final && !finals))
+        return fail(RPQ_ERR_INVALID, "null array");
+    std::unique_ptr<rpq_nfa> h(new rpq_nfa());
+    Automaton &a = h->a;
+    a.S = n_states;
+    a.L = n_labels;
+    for (int32_t i = 0; i < n_trans; i++) {
+        if (from[i] < 0 || from[i] >= n_states || to[i] < 0 || to[i] >= n_states)
+            return fail(RPQ_ERR_INVALID, "transition %d: state out of range", i);
+        if (label[i] < 0 || label[i] >= 2 * n_labels)
+            return fail(RPQ_ERR_INVALID, "transition %d: label %d outside [0, %d)", i, label[i],
+                        2 * n_labels);
+        a.from.push_back(from[i]);
+        a.to.push_back(to[i]);
+        a.sym.push_back(label[i]);
+    }
+    for (int32_t i = 0; i < n_start; i++) {
+        if (starts[i] < 0 || starts[i] >= n_states) return fail(RPQ_ERR_INVALID, "start state out of range");
+        a.start_mask |= 1ull << starts[i];
+    }
+    for (int32_t i = 0; i < n_final; i++) {
+        if (finals[i] < 0 || finals[i] >= n_states) return fail(RPQ_ERR_INVALID, "final state out of range");
+        a.final_mask |= 1ull << finals[i];
+    }
+    *out = h.release();
+    return RPQ_OK;
+}
+
+extern "C" void rpq_nfa_free(rpq_nfa *nfa) { delete nfa; }
+
+extern "C" rpq_status rpq_nfa_info(const rpq_nfa *nfa, int32_t *n_states, int32_t *n_trans,
+                                   int32_t *n_labels) {
+    clear_error();
+    if (!nfa) return fail(RPQ_ERR_INVALID, "nfa is null");
+    if (n_states) *n_states = nfa->a.S;
+    if (n_trans) *n_trans = (int32_t)nfa->a.from.size();
+    if (n_labels) *n_labels = nfa->a.L;
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_nfa_export(const rpq_nfa *nfa, int32_t *from, int32_t *to, int32_t *label,
+                                     int32_t capacity, uint64_t *start_mask, uint64_t *final_mask) {
+    clear_error();
+    if (!nfa) return fail(RPQ_ERR_INVALID, "nfa is null");
+    const int32_t T = (int32_t)nfa->a.from.size();
+    if (start_mask) *start_mask = nfa->a.start_mask;
+    if (final_mask) *final_mask = nfa->a.final_mask;
+    if (capacity < T) return fail(RPQ_ERR_CAPACITY, "need %d transitions", T);
+    for (int32_t i = 0; i < T; i++) {
+        if (from) from[i] = nfa->a.from[i];
+        if (to) to[i] = nfa->a.to[i];
+        if (label) label[i] = nfa->a.sym[i];
+    }
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_nfa_accepts(const rpq_nfa *nfa, const int32_t *word, int32_t length,
+                                      int32_t *accepted) {
+    clear_error();
+    if (!nfa || !accepted || (length > 0 && !word)) return fail(RPQ_ERR_INVALID, "null argument");
+    if (length < 0) return fail(RPQ_ERR_INVALID, "negative length");
+    *accepted = automaton_accepts(nfa->a, word, length) ? 1 : 0;
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_nfa_reverse(const rpq_nfa *nfa, rpq_nfa **out) {
+    clear_error();
+    if (!nfa || !out) return fail(RPQ_ERR_INVALID, "null argument");
+    std::unique_ptr<rpq_nfa> h(new rpq_nfa());
+    h->a = automaton_reverse(nfa->a);
+    *out = h.release();
+    return RPQ_OK;
+}
+
+// --------------------------------------------------------------- query --
+
+extern "C" rpq_status rpq_query(const rpq_graph *g, const rpq_nfa *nfa, int32_t source,
+                                int32_t max_levels, int32_t *out_vertices, int64_t capacity,
+                                int64_t *out_count, rpq_stats *stats, void *stream) {
+    clear_error();
+    if (!g || !nfa || !out_count) return fail(RPQ_ERR_INVALID, "null argument");
+    if (capacity < 0 || (capacity > 0 && !out_vertices))
+        return fail(RPQ_ERR_INVALID, "bad output buffer");
+    *out_count = 0;
+    rpq_graph *gm = const_cast<rpq_graph *>(g);
+    const bool dev = out_vertices && is_device_pointer(out_vertices);
+    int64_t count = 0;
+    rpq_status s = run_query(gm, nfa->a, source, max_levels, dev ? out_vertices : nullptr, capacity,
+                             nullptr, dev ? nullptr : out_vertices, stats, &count, stream);
+    if (s != RPQ_OK) return s;
+    *out_count = count;
+    if (count > capacity)
+        return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices, capacity %lld", (long long)count,
+                    (long long)capacity);
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_query_bitset(const rpq_graph *g, const rpq_nfa *nfa, int32_t source,
+                                       int32_t max_levels, uint64_t *out_bits, int64_t *out_count,
+                                       rpq_stats *stats, void *stream) {
+    clear_error();
+    if (!g || !nfa || !out_bits || !out_count) return fail(RPQ_ERR_INVALID, "null argument");
+    rpq_graph *gm = const_cast<rpq_graph *>(g);
+    int32_t n = 0;
+    rpq_status s = rpq_graph_info(g, -1, &n, nullptr, nullptr);
+    if (s != RPQ_OK) return s;
+    const size_t words = ((size_t)n + 63) / 64;
+    int64_t count = 0;
+    if (is_device_pointer(out_bits)) {
+        s = run_query(gm, nfa->a, source, max_levels, nullptr, 0, out_bits, nullptr, stats, &count,
+                      stream);
+    } else {
+        DevBuf tmp;
+        if (!tmp.alloc(words * sizeof(uint64_t))) return fail(RPQ_ERR_OOM, "bitset buffer");
+        s = run_query(gm, nfa->a, source, max_levels, nullptr, 0, tmp.as<uint64_t>(), nullptr,
+                      stats, &count, stream);
+        if (s == RPQ_OK) {
+            cudaStream_t st = static_cast<cudaStream_t>(stream);
+            if (cudaMemcpyAsync(out_bits, tmp.p, words * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return fail(RPQ_ERR_CUDA, "bitset copy: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+    }
+    if (s != RPQ_OK) return s;
+    *out_count = count;
+    return RPQ_OK;
+}
+

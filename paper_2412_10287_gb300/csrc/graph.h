@@ -1,0 +1,40 @@
+// The device-resident graph: per-label Boolean decomposition {G^a} (section 3
+// of the paper) stored as CSR (rows = sources) and CSC (rows = destinations).
+#pragma once
+
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rpq {
+
+// Query workspaces are cached on the graph so repeated queries do not
+// allocate; each concrete workspace type derives from this.
+struct WorkspaceBase {
+    virtual ~WorkspaceBase() = default;
+};
+
+}  // namespace rpq
+
+struct rpq_graph {
+    int32_t n = 0;           // vertices
+    int32_t L = 0;           // labels
+    int64_t m_input = 0;     // COO entries given
+    int64_t m_unique = 0;    // distinct (src, dst, label) triples
+    int device = 0;
+    // adjacency of label direction d in [0, 2L): d < L -> CSR of G^d (out-rows);
+    // d >= L -> CSC of G^{d-L} (in-rows), i.e. the out-rows of G^{(d-L)^-}.
+    std::vector<rpq::DevAdj> adj;
+    std::vector<int64_t> nnz;  // distinct edges per label
+    rpq::DevBuf d_adj;         // device copy of adj
+    rpq::DevBuf csr_nbr, csc_nbr;  // distinct neighbour ids, label-major
+    std::vector<std::unique_ptr<rpq::DevBuf>> owned;  // offsets / hypersparse rows
+
+    std::mutex ws_mu;
+    std::vector<std::unique_ptr<rpq::WorkspaceBase>> ws_free;
+
+    // direction whose rows are the in-rows of direction d (for pull)
+    int32_t inverse_dir(int32_t d) const { return d < L ? d + L : d - L; }
+};

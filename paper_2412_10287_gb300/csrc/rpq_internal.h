@@ -1,0 +1,70 @@
+// Internal declarations shared by the translation units of librpq.so.
+#pragma once
+
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "rpq.h"
+
+namespace rpq {
+
+// ----------------------------------------------------------------- errors --
+// Records a message for rpq_last_error() on this thread and returns `st`.
+rpq_status fail(rpq_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+void clear_error();
+
+// ------------------------------------------------------------- allocator --
+void *dev_alloc(size_t bytes);  // nullptr on failure
+void dev_free(void *p);
+
+// RAII device buffer from the library allocator.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { reset(); }
+    bool alloc(size_t b) {
+        reset();
+        if (b == 0) b = 16;
+        p = dev_alloc(b);
+        bytes = p ? b : 0;
+        return p != nullptr;
+    }
+    void reset() {
+        if (p) dev_free(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------- host automaton --
+constexpr int kMaxStates = 64;
+
+struct Automaton {
+    int32_t S = 0;  // number of states (<= 64)
+    int32_t L = 0;  // number of graph labels; symbols are in [0, 2L)
+    std::vector<int32_t> from, to, sym;
+    uint64_t start_mask = 0, final_mask = 0;
+};
+
+// Regex -> minimised DFA; returns RPQ_OK or an error (message recorded).
+rpq_status compile_regex(const char *text, int32_t n_labels, Automaton *out);
+bool automaton_accepts(const Automaton &a, const int32_t *word, int32_t len);
+Automaton automaton_reverse(const Automaton &a);
+
+// Single query (query.cu).  See run_query there for the output contract.
+rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
+                     int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
+                     int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream);
+
+}  // namespace rpq
+
+struct rpq_nfa {
+    rpq::Automaton a;
+};
