@@ -56,26 +56,48 @@ typedef struct {
     int32_t *nbr; /* neighbour vertex */
 } adjlist_t;
 
+static int cmp_u64(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
 /* Adjacency lists: entry (a, w) in row v for every edge v -a-> w, and entry
- * (a + L, u) in row v for every edge u -a-> v. */
+ * (a + L, u) in row v for every edge u -a-> v.  A repeated (u, v, a) triple
+ * is kept once: the edge set E is a set (section 2) and G^a is a Boolean
+ * matrix (section 3), so degrees count distinct neighbours per label. */
 static int build_adjacency(int32_t n, int32_t L, int64_t m, const int32_t *src,
                            const int32_t *dst, const int32_t *lab, adjlist_t *g) {
+    int64_t *off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(2 * m + 1));
     g->off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     g->lab = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
     g->nbr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
-    if (!g->off || !g->lab || !g->nbr) return ORC_ENOMEM;
-    for (int64_t i = 0; i < m; i++) { g->off[src[i] + 1]++; g->off[dst[i] + 1]++; }
-    for (int32_t v = 0; v < n; v++) g->off[v + 1] += g->off[v];
+    if (!off || !key || !g->off || !g->lab || !g->nbr) { free(off); free(key); return ORC_ENOMEM; }
+    for (int64_t i = 0; i < m; i++) { off[src[i] + 1]++; off[dst[i] + 1]++; }
+    for (int32_t v = 0; v < n; v++) off[v + 1] += off[v];
     int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
-    if (!fill) return ORC_ENOMEM;
-    memcpy(fill, g->off, sizeof(int64_t) * (size_t)(n + 1));
+    if (!fill) { free(off); free(key); return ORC_ENOMEM; }
+    memcpy(fill, off, sizeof(int64_t) * (size_t)(n + 1));
     for (int64_t i = 0; i < m; i++) {
-        int64_t p = fill[src[i]]++;
-        g->lab[p] = lab[i]; g->nbr[p] = dst[i];
-        p = fill[dst[i]]++;
-        g->lab[p] = lab[i] + L; g->nbr[p] = src[i];
+        key[fill[src[i]]++] = ((uint64_t)(uint32_t)lab[i] << 32) | (uint32_t)dst[i];
+        key[fill[dst[i]]++] = ((uint64_t)(uint32_t)(lab[i] + L) << 32) | (uint32_t)src[i];
     }
     free(fill);
+    int64_t out = 0;
+    for (int32_t v = 0; v < n; v++) {
+        const int64_t b = off[v], e = off[v + 1];
+        qsort(key + b, (size_t)(e - b), sizeof(uint64_t), cmp_u64);
+        g->off[v] = out;
+        for (int64_t k = b; k < e; k++) {
+            if (k > b && key[k] == key[k - 1]) continue;
+            g->lab[out] = (int32_t)(key[k] >> 32);
+            g->nbr[out] = (int32_t)(key[k] & 0xffffffffu);
+            out++;
+        }
+    }
+    g->off[n] = out;
+    free(off);
+    free(key);
     return ORC_OK;
 }
 

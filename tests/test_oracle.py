@@ -331,6 +331,21 @@ def test_counters_two_state_dfa_on_star():
     assert c["push_bytes"] == (8 + 4 * k) + k * (8 + 4) + (8 + 0)
 
 
+@pytest.mark.parametrize("seed", range(10))
+def test_duplicate_edges_change_nothing(seed):
+    """E is a set and G^a Boolean: repeating every triple leaves the answer
+    and every counter unchanged."""
+    g = W.tiny_graph(seed + 2100, max_n=10, max_m=20)
+    S, trans, starts, finals = W.tiny_automaton(seed + 2101, g.n_labels, 4, 10)
+    nfa = nfa_from_lists(S, trans, starts, finals, g.n_labels)
+    g2 = W.Graph("dup", g.n, g.n_labels, np.concatenate([g.src, g.src[::-1]]),
+                 np.concatenate([g.dst, g.dst[::-1]]), np.concatenate([g.lab, g.lab[::-1]]))
+    for s in range(g.n):
+        a, b = answer(g, nfa, s), answer(g2, nfa, s)
+        assert a["answer"].tolist() == b["answer"].tolist()
+        assert a["counters"] == b["counters"]
+
+
 # ---------------------------------------------------------------- golden ---
 
 def _load_fixture(name):
