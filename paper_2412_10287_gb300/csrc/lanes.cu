@@ -16,8 +16,10 @@
 //           the touched list becomes the next frontier list.
 // The answer of lane i is {v : P[v][k] has bit i for a final slot k of i}.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -350,7 +352,7 @@ __global__ void lane_count_kernel(const uint32_t *__restrict__ A32, int64_t word
     if (id >= (long long)n_lanes * chunks) return;
     const int ln = (int)(id / chunks);
     const long long ch = id % chunks;
-    const long long w0 = ch * kCountChunk, w1 = min(words32, w0 + kCountChunk);
+    const long long w0 = ch * kCountChunk, w1 = (long long)min((long long)words32, (long long)(w0 + kCountChunk));
     long long c = 0;
     for (long long w = w0 + threadIdx.x; w < w1; w += blockDim.x)
         c += __popc(A32[(size_t)ln * words32 + w]);
@@ -372,7 +374,7 @@ __global__ void lane_write_kernel(const uint32_t *__restrict__ A32, int64_t word
     if (id >= (long long)n_lanes * chunks) return;
     const int ln = (int)(id / chunks);
     const long long ch = id % chunks;
-    const long long w0 = ch * kCountChunk, w1 = min(words32, w0 + kCountChunk);
+    const long long w0 = ch * kCountChunk, w1 = (long long)min((long long)words32, (long long)(w0 + kCountChunk));
     __shared__ long long wsum[33];
     long long run = pos[id];
     const unsigned lane = lane_id();
@@ -607,7 +609,10 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     auto put = [&](const void *p, size_t bytes) {
         off = (off + 15) & ~size_t(15);
         const size_t at = off;
-        if (bytes) memcpy(hs + at, p, bytes);
+        if (bytes && at + bytes <= ws->staging_bytes) {
+            if (p) memcpy(hs + at, p, bytes);
+            else memset(hs + at, 0, bytes);
+        }
         off += bytes;
         return at;
     };
@@ -623,7 +628,6 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
         lane_ws_release(g, std::move(ws));
         return fail(RPQ_ERR_INVALID, "lane tables too large");
     }
-    memset(hs + o_last, 0, sizeof(int32_t) * kLanes);
     uint8_t *dt = ws->tables.as<uint8_t>();
     RPQ_CUDA_TRY(cudaMemcpyAsync(dt, hs, off, cudaMemcpyHostToDevice, st));
     const size_t words = (size_t)g->n * K * kLW;
@@ -761,8 +765,6 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     lane_ws_release(g, std::move(ws));
     return RPQ_OK;
 }
-
-bool is_device_pointer(const void *p);
 
 }  // namespace rpq
 

@@ -2,24 +2,26 @@
 //     M <- ( OR_a (N^a)^T x M x G^a ) <not P>,  P <- P + M,  until M = 0;
 //     answer F x P
 // run as ONE persistent cooperative kernel per query.  The Boolean matrices
-// are kept as bitsets (one row of |V| bits per automaton state) plus, for the
-// frontier M, per-state vertex lists.  Each level is two grid-wide phases:
+// are bitsets with one row of |V| bits per automaton state (P: visited,
+// F_j: the frontier M_j), and the frontier is also kept as per-state vertex
+// lists.  Each level j is one grid-wide phase followed by one grid barrier:
 //
-//   expand  for every (label direction d, target state q'):
-//             push  -- for every frontier pair (q, v) with q -d-> q' and every
-//                      w in row v of G^d: if w not in P[q'], set NX[q'][w]
-//                      (atomicOr); rows are spread over a CTA by a scan-based
-//                      gather, hub rows over many CTAs in fixed chunks;
-//             pull  -- for every w not in P[q'] with in-edges of direction d:
-//                      NX[q'][w] = OR over in-neighbours u of
-//                      X_{d,q'}[u] = OR_{q: q -d-> q'} M[q][u]  (early exit);
-//           the chosen direction per (d, q') follows the edge mass of the
-//           frontier (a direction-optimising BFS: push-pull is the
-//           optimisation the paper's conclusion names).
-//   commit  for every word first set this level (a touched-word list):
-//             M[q'] = NX word (already masked by not P), P |= M, NX = 0; the
-//             new frontier pairs become vertex lists with their row lengths
-//             (edge mass for the next direction choice, hub rows split off).
+//   expand j   for every (label direction d, target state q'):
+//     push     for every frontier pair (q, v) with q -d-> q' and every w in
+//              row v of G^d: atomicOr P[q'][w]; the lane that flips the bit
+//              from 0 has discovered (q', w) in M_{j+1} (it was not in P_j,
+//              the mask <not P> of Algorithm 1) and appends it;
+//     pull     for every w not in P[q'] with in-edges of direction d: one
+//              in-neighbour u with X_{d,q'}[u] = OR_{q: q -d-> q'} M_j[q][u]
+//              suffices (early exit); then the same atomicOr discovery.
+//   A discovered pair is appended to the frontier list of q', its bit set in
+//   F_{j+1}, and the rows it will expand are measured: their edge mass steers
+//   the next push/pull choice (a direction-optimising BFS: the push-pull
+//   optimisation the paper's conclusion names); rows of >= kWarpRow edges go
+//   to a chunk list that every warp of the grid draws 128-edge chunks from,
+//   shorter rows are expanded by a CTA-wide scan-based gather.
+//   decide j+1 (every CTA, same data): stop when M_{j+1} is empty or the level
+//   cap is reached; else pick push or pull per (d, q').
 //
 // Every wait on other CTAs (the grid barrier) is bounded by a wall-clock
 // limit; on expiry the kernel records RPQ_ERR_TIMEOUT and returns.
@@ -36,13 +38,14 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kHubDeg = 4096;    // rows at least this long are split across CTAs
-constexpr int kHubChunk = 2048;  // edges per hub chunk
-constexpr int kGather = 1024;    // gather buffer entries per CTA
-constexpr int kWarpRow = 32;     // rows at least this long are expanded by a whole warp
+constexpr int kR = 4;                 // edges per lane per round in the batched loops
+constexpr int kWarpRow = 32;          // rows with at least this many edges are chunked
+constexpr int kChunk = 32 * kR;       // edges per chunk: one warp round
+constexpr int kClaimChunks = 4;       // chunks a warp claims at once
+constexpr int kGather = 1024;         // gather buffer entries per CTA
 constexpr int kMaxGroups = 512;
 constexpr int kMaxUnits = 512;
-constexpr int kMaxTargets = 4096;
+constexpr int kMaxTargets = 2048;
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;
 
 // (source state q, direction d) with the targets delta(q, d) as a mask.
@@ -60,35 +63,34 @@ struct QUnit {
     int64_t in_nnz;
 };
 
-struct Hub {
+// A long row of a frontier pair: group g, vertex v, edges [b, e), and the
+// index of its first chunk.
+struct Row {
     int32_t g, v, b, e;
-    int64_t chunk_base;
+    long long chunk0;
 };
 
-// Device counters of one query (zeroed by the kernel prologue except the
-// barrier fields, which the host zeroes at workspace creation).
+// Device counters of one query.  Per-level fields rotate over 3 slots:
+// slot j % 3 holds level j.
 struct Counters {
     unsigned bar_count, bar_gen;
-    int32_t status, where;
-    unsigned long long touched[3];
-    unsigned long long fl_count[2][kMaxStates];
-    unsigned long long lvl_bytes[2], lvl_edges[2];
-    unsigned long long hub_packed[2];  // (entries << 40) | chunks
-    unsigned long long claim_hub[2], claim_item[2], claim_pull[2];
+    int32_t status, pad0;
+    unsigned long long fl_count[3][kMaxStates];  // frontier pairs per state
+    unsigned long long rows_packed[3];           // (rows << 40) | chunks
+    unsigned long long lvl_bytes[3], lvl_edges[3];
+    unsigned long long claim_chunk[3], claim_item[3], claim_pull[3];
     long long levels, visited, expanded, product_edges, push_bytes;
     long long push_units, pull_units, answer_count;
-    long long final_flag;
 };
 
 struct KParams {
-    // graph
     const DevAdj *adj;
     int32_t n, W, S;
-    int32_t n_groups, n_units, n_targets;
+    int32_t n_groups, n_units, n_targets, n_ugroups;
     int32_t source, max_levels;
     uint64_t start_mask, final_mask;
-    float alpha;       // pull when frontier edge mass * alpha > in-adjacency edges
-    int32_t min_pull;  // ... and the unit's source frontier has at least this many pairs
+    float alpha;       // pull when frontier edge mass * alpha > in-adjacency edges + rows
+    int32_t min_pull;  // ... and the unit's source frontier holds at least this many pairs
     // automaton tables (device)
     const QGroup *groups;
     const QUnit *units;
@@ -96,19 +98,31 @@ struct KParams {
     const int32_t *t_state;  // per target slot: q'
     const int32_t *u_group;  // per unit group slot: group index
     // state (device)
-    uint64_t *P, *NX, *F0, *F1;
-    uint32_t *T0, *T1, *T2;
-    int32_t *FL0, *FL1;    // [S][n]
-    Hub *H0, *H1;
-    int64_t hub_cap;
-    unsigned long long *mf;  // [2][kMaxGroups]
+    uint64_t *P;             // [S][W]
+    uint64_t *F[3];          // [S][W] per level slot
+    int32_t *FL[3];          // [S][n] per level slot
+    Row *rows[3];            // long rows per level slot
+    int32_t *cmap[3];        // chunk -> row index per level slot
+    long long row_cap, chunk_cap;
+    unsigned long long *mf;  // [3][kMaxGroups]: frontier edge mass per group
     long long *fin_sums;     // [gridDim]
     Counters *c;
     // output
     int32_t *out_list;
     int64_t capacity;
     uint64_t *out_bits;  // bitset output (or nullptr)
+    // optional per-level trace (block 0's view)
+    unsigned long long *trace;
+    int32_t trace_cap;
 };
+
+constexpr int kTraceFields = 8;  // t_decide, t_expand, t_barrier, pairs, push units, pull units
+constexpr int kTraceLevels = 4096;
+
+__device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsigned long long v) {
+    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0 && j < p.trace_cap)
+        p.trace[(size_t)j * kTraceFields + f] = v;
+}
 
 // ------------------------------------------------------------ barrier ----
 __device__ __forceinline__ int load_status(const Counters *c) {
@@ -130,7 +144,6 @@ __device__ bool grid_barrier(Counters *c) {
             const uint64_t t0 = global_timer_ns();
             unsigned it = 0;
             while (*genp == gen) {
-                __nanosleep(32);
                 if ((++it & 255u) == 0) {
                     if (load_status(c) != 0) break;
                     if (global_timer_ns() - t0 > kBarrierTimeoutNs) {
@@ -146,273 +159,379 @@ __device__ bool grid_barrier(Counters *c) {
     return load_status(c) == 0;
 }
 
-// ------------------------------------------------------- warp helpers ----
-// Appends `code` for every lane with `need`; all 32 lanes must call.
-__device__ __forceinline__ void warp_append(bool need, uint32_t code, uint32_t *list,
-                                            unsigned long long *count) {
-    const unsigned m = __ballot_sync(kFull, need);
-    if (!m) return;
-    const int leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if ((int)lane_id() == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
-    base = __shfl_sync(kFull, base, leader);
-    if (need) list[base + __popc(m & lanemask_lt())] = code;
+// ------------------------------------------------------- shared layout ---
+// Per-query tables live in shared memory for the whole kernel, so that the
+// per-level control work never waits on global memory.
+struct Shared {
+    uint64_t *tpush;    // push-mode targets of each group (decided per level)
+    long long *gpref;   // prefix of frontier items over push groups (n_groups + 1)
+    const int32_t **gnbr;
+    int32_t *gq, *gd, *gtpop;
+    int32_t *gt_first, *gt_count;
+    long long *upref;   // prefix of pull rows over pull units (n_units + 1)
+    long long *urows, *unnz;
+    int32_t *ug_first, *ug_count, *uq2, *uin;
+    uint64_t *usmask;
+    uint8_t *upull;
+    int32_t *t_unit, *t_state, *u_group;
+    unsigned long long *fl;       // [kMaxStates] pairs per state at the current level
+    unsigned long long *fl_prev;  // [kMaxStates] at the previous level
+    unsigned long long *mfv;      // [n_groups]
+    unsigned long long *s_mf;     // [n_groups] per-CTA edge mass of discoveries
+    int32_t *gbuf_k;
+    int16_t *gbuf_g;
+};
+
+template <class F>
+__host__ __device__ size_t shared_layout(int ng, int nu, int nt, int nug, F take) {
+    take(0, sizeof(uint64_t) * ng);
+    take(1, sizeof(long long) * (ng + 1));
+    take(2, sizeof(void *) * ng);
+    take(3, sizeof(int32_t) * ng);
+    take(4, sizeof(int32_t) * ng);
+    take(5, sizeof(int32_t) * ng);
+    take(6, sizeof(int32_t) * ng);
+    take(7, sizeof(int32_t) * ng);
+    take(8, sizeof(long long) * (nu + 1));
+    take(9, sizeof(long long) * nu);
+    take(10, sizeof(long long) * nu);
+    take(11, sizeof(int32_t) * nu);
+    take(12, sizeof(int32_t) * nu);
+    take(13, sizeof(int32_t) * nu);
+    take(14, sizeof(int32_t) * nu);
+    take(15, sizeof(uint64_t) * nu);
+    take(16, nu);
+    take(17, sizeof(int32_t) * nt);
+    take(18, sizeof(int32_t) * nt);
+    take(19, sizeof(int32_t) * nug);
+    take(20, sizeof(unsigned long long) * kMaxStates);
+    take(21, sizeof(unsigned long long) * kMaxStates);
+    take(22, sizeof(unsigned long long) * ng);
+    take(23, sizeof(unsigned long long) * ng);
+    take(24, sizeof(int32_t) * kGather);
+    return take(25, sizeof(int16_t) * kGather);
 }
 
-// Relaxation of edge (., w) into every target state in `tmask` (already
-// restricted to push-mode targets).  All 32 lanes must call; lanes with
-// valid = false take part in the collectives only.
-__device__ __forceinline__ void relax(const KParams &p, bool valid, uint64_t tmask, int32_t w,
-                                      uint32_t *tl, unsigned long long *tcount) {
-    uint64_t todo = valid ? tmask : 0ull;
-    // iterate over the union of target bits across the warp
-    uint32_t lo = __reduce_or_sync(kFull, (uint32_t)todo);
-    uint32_t hi = __reduce_or_sync(kFull, (uint32_t)(todo >> 32));
+__host__ __device__ size_t shared_bytes(int ng, int nu, int nt, int nug) {
+    size_t off = 0;
+    return shared_layout(ng, nu, nt, nug, [&](int, size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        off += bytes;
+        return off;
+    }) + 16;
+}
+
+__device__ Shared carve(const KParams &p, uint8_t *base) {
+    Shared s;
+    uint8_t *ptr[26];
+    size_t off = 0;
+    shared_layout(p.n_groups, p.n_units, p.n_targets, p.n_ugroups, [&](int i, size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        ptr[i] = base + off;
+        off += bytes;
+        return off;
+    });
+    s.tpush = (uint64_t *)ptr[0];
+    s.gpref = (long long *)ptr[1];
+    s.gnbr = (const int32_t **)ptr[2];
+    s.gq = (int32_t *)ptr[3];
+    s.gd = (int32_t *)ptr[4];
+    s.gtpop = (int32_t *)ptr[5];
+    s.gt_first = (int32_t *)ptr[6];
+    s.gt_count = (int32_t *)ptr[7];
+    s.upref = (long long *)ptr[8];
+    s.urows = (long long *)ptr[9];
+    s.unnz = (long long *)ptr[10];
+    s.ug_first = (int32_t *)ptr[11];
+    s.ug_count = (int32_t *)ptr[12];
+    s.uq2 = (int32_t *)ptr[13];
+    s.uin = (int32_t *)ptr[14];
+    s.usmask = (uint64_t *)ptr[15];
+    s.upull = (uint8_t *)ptr[16];
+    s.t_unit = (int32_t *)ptr[17];
+    s.t_state = (int32_t *)ptr[18];
+    s.u_group = (int32_t *)ptr[19];
+    s.fl = (unsigned long long *)ptr[20];
+    s.fl_prev = (unsigned long long *)ptr[21];
+    s.mfv = (unsigned long long *)ptr[22];
+    s.s_mf = (unsigned long long *)ptr[23];
+    s.gbuf_k = (int32_t *)ptr[24];
+    s.gbuf_g = (int16_t *)ptr[25];
+    return s;
+}
+
+__device__ void load_tables(const KParams &p, const Shared &sh) {
+    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
+        const QGroup G = p.groups[g];
+        sh.gq[g] = G.q;
+        sh.gd[g] = G.d;
+        sh.gnbr[g] = p.adj[G.d].nbr;
+        sh.gtpop[g] = __popcll(G.tmask);
+        sh.gt_first[g] = G.t_first;
+        sh.gt_count[g] = G.t_count;
+        sh.tpush[g] = 0;
+        sh.s_mf[g] = 0;
+    }
+    for (int u = threadIdx.x; u < p.n_units; u += kThreads) {
+        const QUnit U = p.units[u];
+        sh.urows[u] = U.in_rows;
+        sh.unnz[u] = U.in_nnz;
+        sh.ug_first[u] = U.g_first;
+        sh.ug_count[u] = U.g_count;
+        sh.uq2[u] = U.q2;
+        sh.uin[u] = U.in_dir;
+        sh.usmask[u] = U.smask;
+        sh.upull[u] = 0;
+    }
+    for (int i = threadIdx.x; i < p.n_targets; i += kThreads) {
+        sh.t_unit[i] = p.t_unit[i];
+        sh.t_state[i] = p.t_state[i];
+    }
+    for (int i = threadIdx.x; i < p.n_ugroups; i += kThreads) sh.u_group[i] = p.u_group[i];
+    for (int q = threadIdx.x; q < kMaxStates; q += kThreads) {
+        sh.fl[q] = 0;
+        sh.fl_prev[q] = 0;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ discovery --
+struct LevelCtx {
+    int slot;                     // slot of the level being discovered
+    int32_t *FL;
+    uint64_t *F;
+    Row *rows;
+    int32_t *cmap;
+    unsigned long long *s_acc;    // [2] per-CTA push bytes / product edges
+};
+
+// Lanes with `found` have discovered the new pair (q2, w) of the next level.
+// Appends it to the frontier list of q2, sets its frontier bit, and measures
+// its rows for every group leaving q2 (gsf[q2] .. gsf[q2+1]).  q2 must be
+// warp-uniform; all 32 lanes must call.
+__device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t *gsf,
+                              const LevelCtx &L, bool found, int q2, int32_t w) {
+    const unsigned m = __ballot_sync(kFull, found);
+    if (!m) return;
+    const unsigned lane = lane_id();
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader)
+        base = atomicAdd(&p.c->fl_count[L.slot][q2], (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (found) {
+        L.FL[(size_t)q2 * p.n + base + __popc(m & lanemask_lt())] = w;
+        atomicOr((unsigned long long *)(L.F + (size_t)q2 * p.W + ((uint32_t)w >> 6)),
+                 1ull << (w & 63));
+    }
+    unsigned long long acc_b = 0, acc_e = 0;
+    for (int g = gsf[q2]; g < gsf[q2 + 1]; g++) {
+        int32_t rb = 0, re = 0;
+        if (found) adj_row(p.adj[sh.gd[g]], w, rb, re);
+        const int32_t deg = re - rb;
+        if (found) {
+            if (deg) atomicAdd(&sh.s_mf[g], (unsigned long long)deg);
+            acc_b += 8ull + 4ull * (unsigned long long)deg;
+            acc_e += (unsigned long long)deg * (unsigned long long)sh.gtpop[g];
+        }
+        // long rows: warp-aggregated append to the chunk list
+        const bool lng = found && deg >= kWarpRow;
+        const unsigned ml = __ballot_sync(kFull, lng);
+        if (!ml) continue;
+        const int nch = lng ? (deg + kChunk - 1) / kChunk : 0;
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(kFull, incl, 31);
+        const int ld = __ffs(ml) - 1;
+        unsigned long long old = 0;
+        if ((int)lane == ld)
+            old = atomicAdd(&p.c->rows_packed[L.slot],
+                            ((unsigned long long)__popc(ml) << 40) | (unsigned long long)tot);
+        old = __shfl_sync(kFull, old, ld);
+        if (lng) {
+            const long long ri = (long long)(old >> 40) + __popc(ml & lanemask_lt());
+            const long long cb = (long long)(old & ((1ull << 40) - 1)) + (incl - nch);
+            if (ri < p.row_cap && cb + nch <= p.chunk_cap) {
+                L.rows[ri] = Row{g, w, rb, re, cb};
+                for (int k = 0; k < nch; k++) L.cmap[cb + k] = (int32_t)ri;
+            } else {
+                atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
+            }
+        }
+    }
+    if (acc_b) atomicAdd(&L.s_acc[0], acc_b);
+    if (acc_e) atomicAdd(&L.s_acc[1], acc_e);
+}
+
+// General relaxation (any number of target states per lane): edge (., w)
+// into every target in tmask.  All 32 lanes must call.
+__device__ void relax_general(const KParams &p, const Shared &sh, const int32_t *gsf,
+                              const LevelCtx &L, bool valid, uint64_t tmask, int32_t w) {
+    const uint64_t todo = valid ? tmask : 0ull;
+    const uint32_t lo = __reduce_or_sync(kFull, (uint32_t)todo);
+    const uint32_t hi = __reduce_or_sync(kFull, (uint32_t)(todo >> 32));
     uint64_t all = ((uint64_t)hi << 32) | lo;
     const uint32_t wi = (uint32_t)w >> 6;
     const uint64_t bit = 1ull << (w & 63);
     while (all) {
         const int q2 = __ffsll((long long)all) - 1;
         all &= all - 1;
-        bool need = false;
+        bool found = false;
         if ((todo >> q2) & 1ull) {
-            const size_t idx = (size_t)q2 * p.W + wi;
-            if (!(__ldcg(p.P + idx) & bit) && !(__ldcg(p.NX + idx) & bit)) {
-                const unsigned long long old =
-                    atomicOr((unsigned long long *)(p.NX + idx), (unsigned long long)bit);
-                need = (old == 0ull);
+            uint64_t *Pw = p.P + (size_t)q2 * p.W + wi;
+            if (!(__ldcg(Pw) & bit)) {
+                const unsigned long long old = atomicOr((unsigned long long *)Pw, bit);
+                found = !(old & bit);
             }
         }
-        warp_append(need, (uint32_t)q2 * (uint32_t)p.W + wi, tl, tcount);
+        warp_discover(p, sh, gsf, L, found, q2, w);
     }
 }
 
-// ------------------------------------------------------- shared layout ---
-struct Shared {
-    // per group (dynamic arrays carved from extern shared memory)
-    uint64_t *tpush;    // push-mode targets of each group
-    long long *gpref;   // prefix of frontier items over push groups (n_groups + 1)
-    const int32_t **gnbr;
-    int32_t *gq, *gd;
-    // per unit
-    long long *upref;   // prefix of pull rows over pull units (n_units + 1)
-    uint8_t *upull;
-    // gather buffer
-    int32_t *gbuf_k;
-    int16_t *gbuf_g;
-};
-
-__device__ Shared carve(const KParams &p, uint8_t *base) {
-    Shared s;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        off = (off + 15) & ~size_t(15);
-        uint8_t *r = base + off;
-        off += bytes;
-        return r;
-    };
-    s.tpush = (uint64_t *)take(sizeof(uint64_t) * p.n_groups);
-    s.gpref = (long long *)take(sizeof(long long) * (p.n_groups + 1));
-    s.gnbr = (const int32_t **)take(sizeof(void *) * p.n_groups);
-    s.gq = (int32_t *)take(sizeof(int32_t) * p.n_groups);
-    s.gd = (int32_t *)take(sizeof(int32_t) * p.n_groups);
-    s.upref = (long long *)take(sizeof(long long) * (p.n_units + 1));
-    s.upull = (uint8_t *)take(p.n_units);
-    s.gbuf_k = (int32_t *)take(sizeof(int32_t) * kGather);
-    s.gbuf_g = (int16_t *)take(sizeof(int16_t) * kGather);
-    return s;
-}
-
-__host__ __device__ size_t shared_bytes(int n_groups, int n_units) {
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        off = (off + 15) & ~size_t(15);
-        off += bytes;
-    };
-    take(sizeof(uint64_t) * n_groups);
-    take(sizeof(long long) * (n_groups + 1));
-    take(sizeof(void *) * n_groups);
-    take(sizeof(int32_t) * n_groups);
-    take(sizeof(int32_t) * n_groups);
-    take(sizeof(long long) * (n_units + 1));
-    take(n_units);
-    take(sizeof(int32_t) * kGather);
-    take(sizeof(int16_t) * kGather);
-    return off + 64;
+// Batched relaxation: kR edges per lane, loads issued together.  Fast path
+// when every active edge of the warp round has the same single target
+// state (the common case for a DFA).  All 32 lanes must call.
+__device__ __forceinline__ void relax_batch(const KParams &p, const Shared &sh, const int32_t *gsf,
+                                            const LevelCtx &L, const bool (&valid)[kR],
+                                            const uint64_t (&tm)[kR], const int32_t (&w)[kR]) {
+    uint64_t any = 0;
+#pragma unroll
+    for (int r = 0; r < kR; r++) any |= valid[r] ? tm[r] : 0ull;
+    const uint32_t lo = __reduce_or_sync(kFull, (uint32_t)any);
+    const uint32_t hi = __reduce_or_sync(kFull, (uint32_t)(any >> 32));
+    const uint64_t all = ((uint64_t)hi << 32) | lo;
+    if (!all) return;
+    if (all & (all - 1)) {
+#pragma unroll
+        for (int r = 0; r < kR; r++) relax_general(p, sh, gsf, L, valid[r], tm[r], w[r]);
+        return;
+    }
+    const int q2 = __ffsll((long long)all) - 1;
+    uint64_t *Pq = p.P + (size_t)q2 * p.W;
+    bool act[kR];
+    uint64_t pw[kR];
+#pragma unroll
+    for (int r = 0; r < kR; r++) {
+        act[r] = valid[r] && ((tm[r] >> q2) & 1ull);
+        pw[r] = act[r] ? __ldcg(Pq + ((uint32_t)w[r] >> 6)) : ~0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < kR; r++) {
+        act[r] = act[r] && !((pw[r] >> (w[r] & 63)) & 1ull);
+        if (act[r]) {
+            const uint64_t bit = 1ull << (w[r] & 63);
+            const unsigned long long old =
+                atomicOr((unsigned long long *)(Pq + ((uint32_t)w[r] >> 6)), bit);
+            act[r] = !(old & bit);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kR; r++) warp_discover(p, sh, gsf, L, act[r], q2, w[r]);
 }
 
 // ---------------------------------------------------------------- phases -
-// Commit of level j: consume the touched list TL_j.
-__device__ void commit_phase(const KParams &p, int j, const Shared &sh, unsigned long long *s_cnt,
-                             unsigned long long *s_base, unsigned long long *s_mf,
-                             unsigned long long *s_acc) {
-    const uint32_t *tl = (j % 3 == 0) ? p.T0 : (j % 3 == 1) ? p.T1 : p.T2;
-    const unsigned long long nt = *(volatile unsigned long long *)&p.c->touched[j % 3];
-    uint64_t *F = (j & 1) ? p.F1 : p.F0;
-    int32_t *FL = (j & 1) ? p.FL1 : p.FL0;
-    Hub *H = (j & 1) ? p.H1 : p.H0;
-    const int par = j & 1;
-    // zero the count of the list that the next expansion fills: TL_{j+1}
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.c->touched[(j + 1) % 3] = 0;
-    for (int i = threadIdx.x; i < p.n_groups; i += kThreads) s_mf[i] = 0;
-    if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
-    for (int i = threadIdx.x; i < p.S; i += kThreads) s_cnt[i] = 0;
+// Tile claims: the first tile of every CTA is static, later ones come from a
+// counter that therefore starts past the static ones.  CTA-uniform result.
+__device__ __forceinline__ long long claim_block(unsigned long long *ctr, long long *s_claim,
+                                                 bool first, long long tile) {
+    if (first) return (long long)blockIdx.x * tile;
+    if (threadIdx.x == 0)
+        *s_claim = (long long)gridDim.x * tile + (long long)atomicAdd(ctr, (unsigned long long)tile);
     __syncthreads();
-    for (unsigned long long tile = (unsigned long long)blockIdx.x * kThreads; tile < nt;
-         tile += (unsigned long long)gridDim.x * kThreads) {
-        const unsigned long long e = tile + threadIdx.x;
-        int q2 = 0;
-        uint32_t wi = 0;
-        uint64_t word = 0;
-        unsigned long long loc = 0;
-        if (e < nt) {
-            const uint32_t code = __ldcg(tl + e);
-            q2 = (int)(code / (uint32_t)p.W);
-            wi = code - (uint32_t)q2 * (uint32_t)p.W;
-            const size_t idx = (size_t)q2 * p.W + wi;
-            word = __ldcg(p.NX + idx);
-            p.NX[idx] = 0;
-            p.P[idx] = __ldcg(p.P + idx) | word;
-            F[idx] = word;
-            loc = atomicAdd(&s_cnt[q2], (unsigned long long)__popcll(word));
-        }
-        __syncthreads();
-        if (threadIdx.x < p.S) {
-            const unsigned long long c = s_cnt[threadIdx.x];
-            s_base[threadIdx.x] = c ? atomicAdd(&p.c->fl_count[par][threadIdx.x], c) : 0ull;
-            s_cnt[threadIdx.x] = 0;
-        }
-        __syncthreads();
-        if (word) {
-            unsigned long long pos = s_base[q2] + loc;
-            int32_t *list = FL + (size_t)q2 * p.n;
-            uint64_t wd = word;
-            while (wd) {
-                const int b = __ffsll((long long)wd) - 1;
-                wd &= wd - 1;
-                const int32_t v = (int32_t)(wi * 64u + (uint32_t)b);
-                list[pos++] = v;
-                // edge mass of every group leaving state q2, hubs split off
-                for (int g = 0; g < p.n_groups; g++) {
-                    if (sh.gq[g] != q2) continue;
-                    int32_t rb, re;
-                    adj_row(p.adj[sh.gd[g]], v, rb, re);
-                    const int32_t deg = re - rb;
-                    atomicAdd(&s_mf[g], (unsigned long long)deg);
-                    atomicAdd(&s_acc[0], 8ull + 4ull * (unsigned long long)deg);
-                    const uint64_t tm = p.groups[g].tmask;
-                    atomicAdd(&s_acc[1], (unsigned long long)deg * (unsigned long long)__popcll(tm));
-                    if (deg >= kHubDeg) {
-                        const unsigned long long nch = (deg + kHubChunk - 1) / kHubChunk;
-                        const unsigned long long old =
-                            atomicAdd(&p.c->hub_packed[par], (1ull << 40) | nch);
-                        const unsigned long long hi = old >> 40;
-                        if ((long long)hi < p.hub_cap) {
-                            Hub h;
-                            h.g = g; h.v = v; h.b = rb; h.e = re;
-                            h.chunk_base = (long long)(old & ((1ull << 40) - 1));
-                            H[hi] = h;
-                        } else {
-                            atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
-                        }
-                    }
-                }
-            }
-        }
-    }
+    const long long t = *s_claim;
     __syncthreads();
-    for (int i = threadIdx.x; i < p.n_groups; i += kThreads)
-        if (s_mf[i]) atomicAdd(&p.mf[par * kMaxGroups + i], s_mf[i]);
-    if (threadIdx.x == 0) {
-        if (s_acc[0]) atomicAdd(&p.c->lvl_bytes[par], s_acc[0]);
-        if (s_acc[1]) atomicAdd(&p.c->lvl_edges[par], s_acc[1]);
-    }
+    return t;
 }
 
-// Process push edges k in [kb, ke) of group g's neighbour array, one per thread
-// per round; whole-block uniform loop.
-__device__ __forceinline__ void push_range_block(const KParams &p, const Shared &sh, int g,
-                                                 int64_t kb, int64_t ke, uint32_t *tl,
-                                                 unsigned long long *tcount) {
-    const int32_t *nbr = sh.gnbr[g];
-    const uint64_t tm = sh.tpush[g];
-    for (int64_t base = kb; base < ke; base += kThreads) {
-        const int64_t k = base + threadIdx.x;
-        const bool valid = k < ke;
-        const int32_t w = valid ? __ldg(nbr + k) : 0;
-        relax(p, valid, tm, w, tl, tcount);
-    }
-}
-
-__device__ void expand_phase(const KParams &p, int j, const Shared &sh, long long *s_claim) {
-    // this expansion reads level j (written by commit j) and fills TL_{j+1}
-    const int par = j & 1;
-    const uint64_t *F = par ? p.F1 : p.F0;
-    const int32_t *FL = par ? p.FL1 : p.FL0;
-    const Hub *H = par ? p.H1 : p.H0;
-    uint32_t *tl = ((j + 1) % 3 == 0) ? p.T0 : ((j + 1) % 3 == 1) ? p.T1 : p.T2;
-    unsigned long long *tcount = &p.c->touched[(j + 1) % 3];
+__device__ void expand_phase(const KParams &p, int j, const Shared &sh, const int32_t *gsf,
+                             long long *s_claim, unsigned long long *s_acc) {
+    const int cs = j % 3, ns = (j + 1) % 3, os = (j + 2) % 3;
+    const uint64_t *F = p.F[cs];
+    const int32_t *FL = p.FL[cs];
+    LevelCtx L{ns, p.FL[ns], p.F[ns], p.rows[ns], p.cmap[ns], s_acc};
     const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
 
-    // housekeeping for commit j+1 (nothing reads these now)
-    {
-        uint64_t *Fn = par ? p.F0 : p.F1;  // held level j-1: clear its words
-        if (j >= 1) {
-            const uint32_t *old = ((j - 1) % 3 == 0) ? p.T0 : ((j - 1) % 3 == 1) ? p.T1 : p.T2;
-            const unsigned long long no = *(volatile unsigned long long *)&p.c->touched[(j - 1) % 3];
+    // housekeeping: clear F of level j-1 (slot os) through its vertex lists
+    // and reset slot os's counters (nothing else touches slot os now)
+    if (j >= 1) {
+        for (int q = 0; q < p.S; q++) {
+            const unsigned long long cnt = sh.fl_prev[q];
+            const int32_t *lst = p.FL[os] + (size_t)q * p.n;
+            uint64_t *Fo = p.F[os] + (size_t)q * p.W;
             for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
-                 i < no; i += (unsigned long long)gridDim.x * kThreads)
-                Fn[__ldcg(old + i)] = 0;  // code = q * W + wi indexes the bitset directly
-        }
-        if (blockIdx.x == 0) {
-            const int np = par ^ 1;
-            for (int i = threadIdx.x; i < p.S; i += kThreads) p.c->fl_count[np][i] = 0;
-            for (int i = threadIdx.x; i < p.n_groups; i += kThreads) p.mf[np * kMaxGroups + i] = 0;
-            if (threadIdx.x == 0) {
-                p.c->lvl_bytes[np] = 0;
-                p.c->lvl_edges[np] = 0;
-                p.c->hub_packed[np] = 0;
-                p.c->claim_hub[np] = 0;
-                p.c->claim_item[np] = 0;
-                p.c->claim_pull[np] = 0;
-            }
+                 i < cnt; i += (unsigned long long)gridDim.x * kThreads)
+                Fo[(uint32_t)__ldcg(lst + i) >> 6] = 0;
         }
     }
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < p.S; i += kThreads) p.c->fl_count[os][i] = 0;
+        for (int i = threadIdx.x; i < p.n_groups; i += kThreads) p.mf[os * kMaxGroups + i] = 0;
+        if (threadIdx.x == 0) {
+            p.c->rows_packed[os] = 0;
+            p.c->lvl_bytes[os] = 0;
+            p.c->lvl_edges[os] = 0;
+            p.c->claim_chunk[os] = 0;
+            p.c->claim_item[os] = 0;
+            p.c->claim_pull[os] = 0;
+        }
+    }
+    __syncthreads();
 
-    // (1) hub rows, chunked across all CTAs
+    // (1) chunks of long rows: whole warps, kClaimChunks chunks per claim
     {
-        const unsigned long long packed = *(volatile unsigned long long *)&p.c->hub_packed[par];
-        const long long nh = (long long)(packed >> 40);
+        const unsigned long long packed = *(volatile unsigned long long *)&p.c->rows_packed[cs];
         const long long nchunks = (long long)(packed & ((1ull << 40) - 1));
-        for (;;) {
-            if (threadIdx.x == 0) *s_claim = (long long)atomicAdd(&p.c->claim_hub[par], 1ull);
-            __syncthreads();
-            const long long c = *s_claim;
-            __syncthreads();
-            if (c >= nchunks) break;
-            // hub whose chunk range holds c: last entry with chunk_base <= c
-            long long lo = 0, hi = nh - 1;
-            while (lo < hi) {
-                const long long mid = (lo + hi + 1) >> 1;
-                if (__ldcg(&H[mid].chunk_base) <= c) lo = mid; else hi = mid - 1;
+        const long long gwarp = (long long)blockIdx.x * kWarps + warp;
+        const long long nwarps = (long long)gridDim.x * kWarps;
+        const Row *R = p.rows[cs];
+        const int32_t *CM = p.cmap[cs];
+        for (bool first = true; nchunks > 0; first = false) {
+            long long c0;
+            if (first) {
+                c0 = gwarp * kClaimChunks;
+            } else {
+                unsigned long long t = 0;
+                if (lane == 0)
+                    t = atomicAdd(&p.c->claim_chunk[cs], (unsigned long long)kClaimChunks);
+                c0 = nwarps * kClaimChunks + (long long)__shfl_sync(kFull, t, 0);
             }
-            const int g = __ldcg(&H[lo].g);
-            if (sh.tpush[g] == 0) continue;
-            const int64_t b = __ldcg(&H[lo].b), e = __ldcg(&H[lo].e);
-            const int64_t kb = b + (c - __ldcg(&H[lo].chunk_base)) * kHubChunk;
-            const int64_t ke = min(e, kb + kHubChunk);
-            push_range_block(p, sh, g, kb, ke, tl, tcount);
+            if (c0 >= nchunks) break;
+            const long long c1 = min(nchunks, c0 + kClaimChunks);
+            for (long long c = c0; c < c1; c++) {
+                const int ri = __ldcg(CM + c);
+                const int g = __ldcg(&R[ri].g);
+                const uint64_t tmv = sh.tpush[g];
+                if (!tmv) continue;  // warp-uniform
+                const int32_t rb = __ldcg(&R[ri].b), re = __ldcg(&R[ri].e);
+                const long long c0r = __ldcg(&R[ri].chunk0);
+                const int32_t b = rb + (int32_t)((c - c0r) * kChunk);
+                const int32_t e = min(re, b + kChunk);
+                const int32_t *nbr = sh.gnbr[g];
+                bool valid[kR];
+                uint64_t tm[kR];
+                int32_t w[kR];
+#pragma unroll
+                for (int r = 0; r < kR; r++) {
+                    const int32_t k = b + r * 32 + (int32_t)lane;
+                    valid[r] = k < e;
+                    w[r] = valid[r] ? __ldg(nbr + k) : 0;
+                    tm[r] = tmv;
+                }
+                relax_batch(p, sh, gsf, L, valid, tm, w);
+            }
         }
     }
 
-    // (2) frontier items of push groups, tiles of kThreads items
+    // (2) short rows of push groups: CTA tiles of frontier items, scan-based gather
     const long long total_items = sh.gpref[p.n_groups];
-    for (;;) {
-        if (threadIdx.x == 0)
-            *s_claim = (long long)atomicAdd(&p.c->claim_item[par], (unsigned long long)kThreads);
-        __syncthreads();
-        const long long t0 = *s_claim;
-        __syncthreads();
+    for (bool first = true; total_items > 0; first = false) {
+        const long long t0 = claim_block(&p.c->claim_item[cs], s_claim, first, kThreads);
         if (t0 >= total_items) break;
         const long long i = t0 + threadIdx.x;
         int g = -1;
@@ -426,95 +545,68 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, long lon
             g = lo;
             const int32_t v = __ldcg(FL + (size_t)sh.gq[g] * p.n + (i - sh.gpref[g]));
             adj_row(p.adj[sh.gd[g]], v, rb, re);
-            if (re - rb >= kHubDeg) re = rb;  // handled as a hub
+            if (re - rb >= kWarpRow) re = rb;  // expanded through the chunk list
         }
-        int32_t deg = re - rb;
-        // (a) rows of at least kWarpRow edges: one warp per row
-        {
-            bool pending = deg >= kWarpRow;
-            unsigned m;
-            while ((m = __ballot_sync(kFull, pending)) != 0) {
-                const int leader = __ffs(m) - 1;
-                const int gg = __shfl_sync(kFull, g, leader);
-                const int32_t b = __shfl_sync(kFull, rb, leader);
-                const int32_t e = __shfl_sync(kFull, re, leader);
-                if ((int)lane == leader) pending = false;
-                const int32_t *nbr = sh.gnbr[gg];
-                const uint64_t tm = sh.tpush[gg];
-                for (int32_t base = b; base < e; base += 32) {
-                    const int32_t k = base + (int32_t)lane;
-                    const bool valid = k < e;
-                    const int32_t w = valid ? __ldg(nbr + k) : 0;
-                    relax(p, valid, tm, w, tl, tcount);
-                }
-            }
-            if (deg >= kWarpRow) deg = 0;
-        }
-        // (b) short rows: CTA-wide scan-based gather
-        {
-            long long tot = 0;
-            // block exclusive scan of deg
-            __shared__ int32_t wsum[kWarps + 1];
-            int32_t incl = deg;
+        const int32_t deg = re - rb;
+        __shared__ int32_t wsum[kWarps + 1];
+        int32_t incl = deg;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(kFull, incl, o);
-                if ((int)lane >= o) incl += y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t run = 0;
+            for (int x = 0; x < kWarps; x++) {
+                const int32_t s = wsum[x];
+                wsum[x] = run;
+                run += s;
             }
-            if (lane == 31) wsum[threadIdx.x >> 5] = incl;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int32_t run = 0;
-                for (int w = 0; w < kWarps; w++) {
-                    const int32_t s = wsum[w];
-                    wsum[w] = run;
-                    run += s;
-                }
-                wsum[kWarps] = run;
+            wsum[kWarps] = run;
+        }
+        __syncthreads();
+        const int32_t excl = wsum[warp] + incl - deg;
+        const long long tot = wsum[kWarps];
+        __syncthreads();
+        for (long long rbase = 0; rbase < tot; rbase += kGather) {
+            const long long lo = max((long long)excl, rbase);
+            const long long hi = min((long long)excl + deg, rbase + kGather);
+            for (long long r = lo; r < hi; r++) {
+                sh.gbuf_k[r - rbase] = rb + (int32_t)(r - excl);
+                sh.gbuf_g[r - rbase] = (int16_t)g;
             }
             __syncthreads();
-            const int32_t excl = wsum[threadIdx.x >> 5] + incl - deg;
-            tot = wsum[kWarps];
-            __syncthreads();
-            for (long long rbase = 0; rbase < tot; rbase += kGather) {
-                // scatter my edges that fall in [rbase, rbase + kGather)
-                const long long lo = max((long long)excl, rbase);
-                const long long hi = min((long long)excl + deg, rbase + kGather);
-                for (long long r = lo; r < hi; r++) {
-                    sh.gbuf_k[r - rbase] = rb + (int32_t)(r - excl);
-                    sh.gbuf_g[r - rbase] = (int16_t)g;
-                }
-                __syncthreads();
-                const long long cnt = min((long long)kGather, tot - rbase);
-                for (long long base = 0; base < cnt; base += kThreads) {
-                    const long long idx = base + threadIdx.x;
-                    const bool valid = idx < cnt;
-                    int gg = 0;
-                    int32_t w = 0;
-                    uint64_t tm = 0;
-                    if (valid) {
-                        gg = sh.gbuf_g[idx];
-                        w = __ldg(sh.gnbr[gg] + sh.gbuf_k[idx]);
-                        tm = sh.tpush[gg];
+            const long long cnt = min((long long)kGather, tot - rbase);
+            for (long long base = 0; base < cnt; base += (long long)kThreads * kR) {
+                bool valid[kR];
+                uint64_t tm[kR];
+                int32_t w[kR];
+#pragma unroll
+                for (int r = 0; r < kR; r++) {
+                    const long long idx = base + (long long)r * kThreads + threadIdx.x;
+                    valid[r] = idx < cnt;
+                    w[r] = 0;
+                    tm[r] = 0;
+                    if (valid[r]) {
+                        const int gg = sh.gbuf_g[idx];
+                        w[r] = __ldg(sh.gnbr[gg] + sh.gbuf_k[idx]);
+                        tm[r] = sh.tpush[gg];
                     }
-                    relax(p, valid, tm, w, tl, tcount);
                 }
-                __syncthreads();
+                relax_batch(p, sh, gsf, L, valid, tm, w);
             }
+            __syncthreads();
         }
     }
 
     // (3) pull units: sweep the rows of the in-adjacency
     const long long total_rows = sh.upref[p.n_units];
-    for (;;) {
-        if (threadIdx.x == 0)
-            *s_claim = (long long)atomicAdd(&p.c->claim_pull[par], (unsigned long long)kThreads);
-        __syncthreads();
-        const long long t0 = *s_claim;
-        __syncthreads();
+    for (bool first = true; total_rows > 0; first = false) {
+        const long long t0 = claim_block(&p.c->claim_pull[cs], s_claim, first, kThreads);
         if (t0 >= total_rows) break;
         const long long i = t0 + threadIdx.x;
-        // unit of this tile: tiles never straddle units (prefixes are padded to kThreads)
         int u = 0;
         {
             int lo = 0, hi = p.n_units - 1;
@@ -524,14 +616,13 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, long lon
             }
             u = lo;
         }
-        const QUnit U = p.units[u];
-        const DevAdj A = p.adj[U.in_dir];
+        const DevAdj A = p.adj[sh.uin[u]];
+        const int uq2 = sh.uq2[u];
+        const uint64_t usm = sh.usmask[u];
         const long long r = i - sh.upref[u];
-        const bool in_range = r < U.in_rows;
-        int32_t w = 0;
-        int32_t rb = 0, re = 0;
+        int32_t w = 0, rb = 0, re = 0;
         bool cand = false;
-        if (in_range) {
+        if (r < sh.urows[u]) {
             if (A.fmt == ADJ_DENSE) {
                 w = (int32_t)r;
                 rb = __ldg(A.off + w);
@@ -541,18 +632,15 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, long lon
                 rb = __ldg(A.off + r);
                 re = __ldg(A.off + r + 1);
             }
-            const size_t idx = (size_t)U.q2 * p.W + ((uint32_t)w >> 6);
-            const uint64_t bit = 1ull << (w & 63);
-            cand = (re > rb) && !(__ldcg(p.P + idx) & bit) && !(__ldcg(p.NX + idx) & bit);
+            cand = (re > rb) &&
+                   !((__ldcg(p.P + (size_t)uq2 * p.W + ((uint32_t)w >> 6)) >> (w & 63)) & 1ull);
         }
-        // serial scan of up to kWarpRow in-neighbours
-        bool found = false;
-        bool pending = false;
+        bool found = false, pending = false;
         if (cand) {
             const int32_t lim = min(re, rb + kWarpRow);
             for (int32_t k = rb; k < lim && !found; k++) {
                 const int32_t x = __ldg(A.nbr + k);
-                uint64_t sm = U.smask;
+                uint64_t sm = usm;
                 while (sm) {
                     const int q = __ffsll((long long)sm) - 1;
                     sm &= sm - 1;
@@ -564,7 +652,6 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, long lon
             }
             pending = !found && re - rb > kWarpRow;
         }
-        // long rows: the whole warp scans, ballot for a hit, early exit
         {
             unsigned m;
             while ((m = __ballot_sync(kFull, pending)) != 0) {
@@ -577,7 +664,7 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, long lon
                     bool h = false;
                     if (k < e) {
                         const int32_t x = __ldg(A.nbr + k);
-                        uint64_t sm = U.smask;
+                        uint64_t sm = usm;
                         while (sm) {
                             const int q = __ffsll((long long)sm) - 1;
                             sm &= sm - 1;
@@ -599,61 +686,78 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, long lon
                 }
             }
         }
-        // set the found bits
-        {
-            bool need = false;
-            uint32_t code = 0;
-            if (found) {
-                const uint32_t wi = (uint32_t)w >> 6;
-                const size_t idx = (size_t)U.q2 * p.W + wi;
-                const unsigned long long old =
-                    atomicOr((unsigned long long *)(p.NX + idx), 1ull << (w & 63));
-                need = old == 0ull;
-                code = (uint32_t)U.q2 * (uint32_t)p.W + wi;
-            }
-            warp_append(need, code, tl, tcount);
+        bool disc = false;
+        if (found) {
+            const uint64_t bit = 1ull << (w & 63);
+            const unsigned long long old = atomicOr(
+                (unsigned long long *)(p.P + (size_t)uq2 * p.W + ((uint32_t)w >> 6)), bit);
+            disc = !(old & bit);
         }
+        warp_discover(p, sh, gsf, L, disc, uq2, w);
+    }
+
+    // per-CTA sums of this level's discoveries
+    __syncthreads();
+    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
+        const unsigned long long v = sh.s_mf[g];
+        if (v) {
+            atomicAdd(&p.mf[ns * kMaxGroups + g], v);
+            sh.s_mf[g] = 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (s_acc[0]) atomicAdd(&p.c->lvl_bytes[ns], s_acc[0]);
+        if (s_acc[1]) atomicAdd(&p.c->lvl_edges[ns], s_acc[1]);
     }
 }
 
 // Decide for level j (all CTAs compute the same from the same counters).
 // Returns false when the traversal is over.
 __device__ bool decide_phase(const KParams &p, int j, const Shared &sh) {
-    const int par = j & 1;
-    volatile Counters *c = p.c;
+    const int cs = j % 3;
+    for (int q = threadIdx.x; q < kMaxStates; q += kThreads) sh.fl_prev[q] = sh.fl[q];
+    __syncthreads();
+    if (threadIdx.x < p.S)
+        sh.fl[threadIdx.x] = *(volatile unsigned long long *)&p.c->fl_count[cs][threadIdx.x];
+    for (int g = threadIdx.x; g < p.n_groups; g += kThreads)
+        sh.mfv[g] = __ldcg(p.mf + cs * kMaxGroups + g);
+    __shared__ unsigned long long s_lvl[2];
+    if (threadIdx.x == 0) {
+        s_lvl[0] = *(volatile unsigned long long *)&p.c->lvl_bytes[cs];
+        s_lvl[1] = *(volatile unsigned long long *)&p.c->lvl_edges[cs];
+    }
+    __syncthreads();
     long long total = 0;
-    for (int q = 0; q < p.S; q++) total += (long long)c->fl_count[par][q];
+    for (int q = 0; q < p.S; q++) total += (long long)sh.fl[q];
     const bool expand = total > 0 && (p.max_levels == 0 || j < p.max_levels);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         p.c->visited += total;
         if (total > 0 && j > 0) p.c->levels = j;
         if (expand) {
             p.c->expanded += total;
-            p.c->push_bytes += (long long)c->lvl_bytes[par];
-            p.c->product_edges += (long long)c->lvl_edges[par];
+            p.c->push_bytes += (long long)s_lvl[0];
+            p.c->product_edges += (long long)s_lvl[1];
         }
     }
     if (!expand) return false;
-    // direction per unit
     for (int u = threadIdx.x; u < p.n_units; u += kThreads) {
-        const QUnit U = p.units[u];
         unsigned long long mass = 0, pairs = 0;
-        for (int k = 0; k < U.g_count; k++) {
-            const int g = p.u_group[U.g_first + k];
-            mass += __ldcg(p.mf + par * kMaxGroups + g);
-            pairs += c->fl_count[par][sh.gq[g]];
+        for (int k = 0; k < sh.ug_count[u]; k++) {
+            const int g = sh.u_group[sh.ug_first[u] + k];
+            mass += sh.mfv[g];
+            pairs += sh.fl[sh.gq[g]];
         }
-        const bool pull = (double)mass * (double)p.alpha > (double)U.in_nnz + (double)U.in_rows &&
+        const bool pull = (double)mass * (double)p.alpha >
+                              (double)sh.unnz[u] + (double)sh.urows[u] &&
                           (long long)pairs >= p.min_pull;
         sh.upull[u] = pull ? 1 : 0;
     }
     __syncthreads();
     for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
-        const QGroup G = p.groups[g];
         uint64_t tm = 0;
-        for (int k = 0; k < G.t_count; k++) {
-            const int u = p.t_unit[G.t_first + k];
-            if (!sh.upull[u]) tm |= 1ull << p.t_state[G.t_first + k];
+        for (int k = 0; k < sh.gt_count[g]; k++) {
+            const int t = sh.gt_first[g] + k;
+            if (!sh.upull[sh.t_unit[t]]) tm |= 1ull << sh.t_state[t];
         }
         sh.tpush[g] = tm;
     }
@@ -662,14 +766,14 @@ __device__ bool decide_phase(const KParams &p, int j, const Shared &sh) {
         long long acc = 0;
         for (int g = 0; g < p.n_groups; g++) {
             sh.gpref[g] = acc;
-            if (sh.tpush[g]) acc += (long long)c->fl_count[par][sh.gq[g]];
+            if (sh.tpush[g]) acc += (long long)sh.fl[sh.gq[g]];
         }
         sh.gpref[p.n_groups] = acc;
         long long ra = 0, npush = 0, npull = 0;
         for (int u = 0; u < p.n_units; u++) {
             sh.upref[u] = ra;
             if (sh.upull[u]) {
-                ra += (p.units[u].in_rows + kThreads - 1) / kThreads * kThreads;
+                ra += (sh.urows[u] + kThreads - 1) / kThreads * kThreads;
                 npull++;
             } else {
                 npush++;
@@ -703,7 +807,6 @@ __device__ void final_phase(const KParams &p, long long *s_tmp) {
         if (p.out_bits) p.out_bits[wi] = r;
         cnt += __popcll(r);
     }
-    // block sum
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
     if (threadIdx.x == 0) *s_tmp = 0;
     __syncthreads();
@@ -718,15 +821,32 @@ __device__ void final_write(const KParams &p, long long *s_tmp) {
     const int64_t w0 = (int64_t)min((long long)W, (long long)blockIdx.x * per);
     const int64_t w1 = (int64_t)min((long long)W, (long long)(w0 + per));
     __shared__ long long wsum[kWarps + 1];
-    if (threadIdx.x == 0) {
+    __shared__ long long s_pre[kWarps], s_tot[kWarps];
+    {
         long long pre = 0, tot = 0;
-        for (unsigned b = 0; b < gridDim.x; b++) {
-            const long long s = *(volatile long long *)&p.fin_sums[b];
-            if (b < blockIdx.x) pre += s;
-            tot += s;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads) {
+            const long long v = __ldcg(p.fin_sums + b);
+            if (b < blockIdx.x) pre += v;
+            tot += v;
         }
-        *s_tmp = pre;
-        if (blockIdx.x == 0) p.c->answer_count = tot;
+        for (int o = 16; o > 0; o >>= 1) {
+            pre += __shfl_down_sync(kFull, pre, o);
+            tot += __shfl_down_sync(kFull, tot, o);
+        }
+        if (lane_id() == 0) {
+            s_pre[threadIdx.x >> 5] = pre;
+            s_tot[threadIdx.x >> 5] = tot;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long a = 0, t = 0;
+            for (int w = 0; w < kWarps; w++) {
+                a += s_pre[w];
+                t += s_tot[w];
+            }
+            *s_tmp = a;
+            if (blockIdx.x == 0) p.c->answer_count = t;
+        }
     }
     __syncthreads();
     long long run = *s_tmp;
@@ -776,71 +896,109 @@ __device__ void final_write(const KParams &p, long long *s_tmp) {
 
 __global__ void __launch_bounds__(kThreads) rpq_query_kernel(KParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ unsigned long long s_cnt[kMaxStates], s_base[kMaxStates], s_acc[2];
-    __shared__ unsigned long long s_mf[kMaxGroups];
+    __shared__ int32_t s_gsf[kMaxStates + 1];
     __shared__ long long s_claim;
+    __shared__ unsigned long long s_acc[2];
+    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+        p.trace[(size_t)(p.trace_cap) * kTraceFields + 0] = global_timer_ns();
     Shared sh = carve(p, smem);
-    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
-        const QGroup G = p.groups[g];
-        sh.gq[g] = G.q;
-        sh.gd[g] = G.d;
-        sh.gnbr[g] = p.adj[G.d].nbr;
-        sh.tpush[g] = 0;
+    load_tables(p, sh);
+    if (threadIdx.x <= p.S) {
+        int lo = 0, hi = p.n_groups;  // groups are sorted by source state
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sh.gq[mid] < (int)threadIdx.x) lo = mid + 1; else hi = mid;
+        }
+        s_gsf[threadIdx.x] = lo;
     }
-    // prologue: clear P and the frontier bitsets; block 0 seeds level 0
+    if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
+    __syncthreads();
+    // prologue: P = F_0 = Q_S x {v_s}; F_1 = F_2 = 0; counters of all slots
+    // cleared; level 0 lists and rows seeded by warp 0 of CTA 0
+    const uint32_t swi = (uint32_t)p.source >> 6;
+    const uint64_t sbit = 1ull << (p.source & 63);
     const size_t words = (size_t)p.S * p.W;
     for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < words;
          i += (size_t)gridDim.x * kThreads) {
-        p.P[i] = 0;
-        p.F0[i] = 0;
-        p.F1[i] = 0;
+        const int q = (int)(i / p.W);
+        const uint64_t v =
+            ((uint32_t)(i - (size_t)q * p.W) == swi && ((p.start_mask >> q) & 1ull)) ? sbit : 0ull;
+        p.P[i] = v;
+        p.F[0][i] = v;
+        p.F[1][i] = 0;
+        p.F[2][i] = 0;
     }
     if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < 2 * kMaxGroups; i += kThreads) p.mf[i] = 0;
+        for (int i = threadIdx.x; i < 3 * kMaxGroups; i += kThreads) p.mf[i] = 0;
         if (threadIdx.x == 0) {
             Counters *c = p.c;
-            for (int k = 0; k < 3; k++) c->touched[k] = 0;
-            for (int k = 0; k < 2; k++) {
+            for (int k = 0; k < 3; k++) {
                 for (int q = 0; q < kMaxStates; q++) c->fl_count[k][q] = 0;
-                c->lvl_bytes[k] = c->lvl_edges[k] = c->hub_packed[k] = 0;
-                c->claim_hub[k] = c->claim_item[k] = c->claim_pull[k] = 0;
+                c->rows_packed[k] = c->lvl_bytes[k] = c->lvl_edges[k] = 0;
+                c->claim_chunk[k] = c->claim_item[k] = c->claim_pull[k] = 0;
             }
             c->levels = c->visited = c->expanded = c->product_edges = c->push_bytes = 0;
             c->push_units = c->pull_units = c->answer_count = 0;
-            // level 0 = Q_S x {v_s}: seed NX and the touched list TL_0
-            const uint32_t wi = (uint32_t)p.source >> 6;
-            const uint64_t bit = 1ull << (p.source & 63);
-            unsigned long long n0 = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // the bits of F_0 and P were set above; this adds the level-0
+            // lists, edge mass and long rows of every start state
+            LevelCtx L0{0, p.FL[0], p.F[0], p.rows[0], p.cmap[0], s_acc};
             uint64_t sm = p.start_mask;
             while (sm) {
                 const int q = __ffsll((long long)sm) - 1;
                 sm &= sm - 1;
-                p.NX[(size_t)q * p.W + wi] = bit;
-                p.T0[n0++] = (uint32_t)q * (uint32_t)p.W + wi;
+                warp_discover(p, sh, s_gsf, L0, lane_id() == 0, q, p.source);
             }
-            c->touched[0] = n0;
+            __syncwarp();
+            if (threadIdx.x == 0) {
+                p.c->lvl_bytes[0] = s_acc[0];
+                p.c->lvl_edges[0] = s_acc[1];
+                s_acc[0] = s_acc[1] = 0;
+            }
+            for (int g = threadIdx.x; g < p.n_groups; g += 32) {
+                p.mf[g] = sh.s_mf[g];
+                sh.s_mf[g] = 0;
+            }
         }
     }
     if (!grid_barrier(p.c)) return;
+    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+        p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
     for (int j = 0;; j++) {
-        commit_phase(p, j, sh, s_cnt, s_base, s_mf, s_acc);
+        const bool more = decide_phase(p, j, sh);
+        trace_put(p, j, 0, global_timer_ns());
+        if (p.trace && blockIdx.x == 0 && threadIdx.x == 0 && j < p.trace_cap) {
+            unsigned long long tot = 0, npull = 0;
+            for (int q = 0; q < p.S; q++) tot += sh.fl[q];
+            for (int u = 0; u < p.n_units; u++) npull += sh.upull[u];
+            p.trace[(size_t)j * kTraceFields + 3] = tot;
+            p.trace[(size_t)j * kTraceFields + 4] = more ? (unsigned long long)p.n_units - npull : 0;
+            p.trace[(size_t)j * kTraceFields + 5] = more ? npull : 0;
+        }
+        if (!more) break;
+        expand_phase(p, j, sh, s_gsf, &s_claim, s_acc);
+        trace_put(p, j, 1, global_timer_ns());
         if (!grid_barrier(p.c)) return;
-        if (!decide_phase(p, j, sh)) break;
-        expand_phase(p, j, sh, &s_claim);
-        if (!grid_barrier(p.c)) return;
+        trace_put(p, j, 2, global_timer_ns());
     }
+    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+        p.trace[(size_t)(p.trace_cap) * kTraceFields + 2] = global_timer_ns();
     final_phase(p, &s_claim);
     if (!grid_barrier(p.c)) return;
     final_write(p, &s_claim);
+    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+        p.trace[(size_t)(p.trace_cap) * kTraceFields + 3] = global_timer_ns();
 }
 
 // ------------------------------------------------------------ host side --
 
 struct QueryWorkspace : WorkspaceBase {
     int S_cap = 0;
-    int64_t hub_cap = 0;
+    long long row_cap = 0, chunk_cap = 0;
     int32_t n = 0, W = 0;
-    DevBuf P, NX, F0, F1, T0, T1, T2, FL0, FL1, H0, H1, mf, fin, ctr, tables, out_list;
+    DevBuf P, F[3], FL[3], rows[3], cmap[3], mf, fin, ctr, tables, out_list, trace;
     void *staging = nullptr;  // pinned host: tables upload + counters download
     size_t staging_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -854,54 +1012,64 @@ struct QueryWorkspace : WorkspaceBase {
 constexpr size_t kTablesBytes = 256 * 1024;
 
 // Grid of the persistent kernel: every SM holds the same number of CTAs
-// (cooperative launch requires all of them resident).  Computed once per
-// device for the largest automaton tables, so any query fits.
-int g_grid[64];
+// (cooperative launch requires all of them resident).  Computed per device
+// and per shared-memory size (rounded up to 4 KiB) and cached.
+struct GridKey {
+    int device;
+    size_t smem;
+    bool operator<(const GridKey &o) const {
+        return device != o.device ? device < o.device : smem < o.smem;
+    }
+};
+std::map<GridKey, int> g_grid;
 std::mutex g_grid_mu;
+constexpr size_t kMaxDynSmem = 160 * 1024;
 
-rpq_status get_launch_shape(int device, int *grid) {
-    if (device < 0 || device >= 64) return fail(RPQ_ERR_CUDA, "device id %d", device);
+rpq_status get_launch_shape(int device, size_t smem, int *grid) {
     std::lock_guard<std::mutex> lk(g_grid_mu);
-    if (g_grid[device] > 0) {
-        *grid = g_grid[device];
+    smem = (smem + 4095) & ~size_t(4095);
+    if (smem > kMaxDynSmem)
+        return fail(RPQ_ERR_INVALID, "automaton tables need %zu bytes of shared memory", smem);
+    auto it = g_grid.find({device, smem});
+    if (it != g_grid.end()) {
+        *grid = it->second;
         return RPQ_OK;
     }
     int coop = 0, sms = 0;
     RPQ_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     RPQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     if (!coop) return fail(RPQ_ERR_CUDA, "device lacks cooperative launch");
-    const size_t smem = shared_bytes(kMaxGroups, kMaxUnits);
     RPQ_CUDA_TRY(cudaFuncSetAttribute(rpq_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+                                      (int)kMaxDynSmem));
     int per_sm = 0;
     RPQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rpq_query_kernel, kThreads,
                                                                smem));
     if (per_sm <= 0) return fail(RPQ_ERR_CUDA, "query kernel does not fit on an SM");
     const char *cap = getenv("RPQ_CTAS_PER_SM");
     per_sm = std::min(per_sm, cap ? std::max(1, atoi(cap)) : 4);
-    g_grid[device] = sms * per_sm;
-    *grid = g_grid[device];
+    g_grid[{device, smem}] = sms * per_sm;
+    *grid = sms * per_sm;
     return RPQ_OK;
 }
 
-rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, int64_t hub_cap) {
+rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long row_cap,
+                    long long chunk_cap) {
     const int64_t W = ((int64_t)g->n + 63) / 64;
     const size_t bits = sizeof(uint64_t) * (size_t)S_cap * W;
-    const size_t tl = sizeof(uint32_t) * (size_t)S_cap * W;
     const size_t fl = sizeof(int32_t) * (size_t)S_cap * g->n;
     ws->S_cap = S_cap;
-    ws->hub_cap = hub_cap;
+    ws->row_cap = row_cap;
+    ws->chunk_cap = chunk_cap;
     ws->n = g->n;
     ws->W = (int32_t)W;
-    if (!ws->P.alloc(bits) || !ws->NX.alloc(bits) || !ws->F0.alloc(bits) || !ws->F1.alloc(bits) ||
-        !ws->T0.alloc(tl) || !ws->T1.alloc(tl) || !ws->T2.alloc(tl) || !ws->FL0.alloc(fl) ||
-        !ws->FL1.alloc(fl) || !ws->H0.alloc(sizeof(Hub) * hub_cap) ||
-        !ws->H1.alloc(sizeof(Hub) * hub_cap) ||
-        !ws->mf.alloc(sizeof(unsigned long long) * 2 * kMaxGroups) ||
-        !ws->fin.alloc(sizeof(long long) * 152 * 64) || !ws->ctr.alloc(sizeof(Counters)) ||
-        !ws->tables.alloc(kTablesBytes) || !ws->out_list.alloc(sizeof(int32_t) * (size_t)g->n))
-        return fail(RPQ_ERR_OOM, "query workspace (%d states)", S_cap);
-    RPQ_CUDA_TRY(cudaMemset(ws->NX.p, 0, bits));
+    bool ok = ws->P.alloc(bits) && ws->mf.alloc(sizeof(unsigned long long) * 3 * kMaxGroups) &&
+              ws->fin.alloc(sizeof(long long) * 152 * 64) && ws->ctr.alloc(sizeof(Counters)) &&
+              ws->tables.alloc(kTablesBytes) && ws->out_list.alloc(sizeof(int32_t) * (size_t)g->n);
+    for (int k = 0; k < 3 && ok; k++)
+        ok = ws->F[k].alloc(bits) && ws->FL[k].alloc(fl) &&
+             ws->rows[k].alloc(sizeof(Row) * (size_t)row_cap) &&
+             ws->cmap[k].alloc(sizeof(int32_t) * (size_t)chunk_cap);
+    if (!ok) return fail(RPQ_ERR_OOM, "query workspace (%d states)", S_cap);
     RPQ_CUDA_TRY(cudaMemset(ws->ctr.p, 0, sizeof(Counters)));
     ws->staging_bytes = kTablesBytes + sizeof(Counters) + 64;
     RPQ_CUDA_TRY(cudaMallocHost(&ws->staging, ws->staging_bytes));
@@ -910,12 +1078,13 @@ rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, int64_t h
     return RPQ_OK;
 }
 
-std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, int64_t hub_need, rpq_status *st) {
+std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, long long row_need,
+                                           long long chunk_need, rpq_status *st) {
     {
         std::lock_guard<std::mutex> lk(g->ws_mu);
         for (size_t i = 0; i < g->ws_free.size(); i++) {
             auto *w = dynamic_cast<QueryWorkspace *>(g->ws_free[i].get());
-            if (w && w->S_cap >= S && w->hub_cap >= hub_need) {
+            if (w && w->S_cap >= S && w->row_cap >= row_need && w->chunk_cap >= chunk_need) {
                 std::unique_ptr<QueryWorkspace> r(static_cast<QueryWorkspace *>(g->ws_free[i].release()));
                 g->ws_free.erase(g->ws_free.begin() + i);
                 *st = RPQ_OK;
@@ -926,9 +1095,10 @@ std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, int64_t hub_need
     std::unique_ptr<QueryWorkspace> w(new QueryWorkspace());
     int S_cap = 4;
     while (S_cap < S) S_cap *= 2;
-    int64_t hc = 1024;
-    while (hc < hub_need) hc *= 2;
-    *st = ws_alloc(w.get(), g, S_cap, hc);
+    long long rc = 1024, cc = 4096;
+    while (rc < row_need) rc *= 2;
+    while (cc < chunk_need) cc *= 2;
+    *st = ws_alloc(w.get(), g, S_cap, rc, cc);
     if (*st != RPQ_OK) return nullptr;
     return w;
 }
@@ -943,7 +1113,7 @@ struct Tables {
     std::vector<QGroup> groups;
     std::vector<QUnit> units;
     std::vector<int32_t> t_unit, t_state, u_group;
-    int64_t hub_need = 0;
+    long long row_need = 0, chunk_need = 0;
 };
 
 rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
@@ -990,8 +1160,10 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
         }
         G.t_count = (int32_t)t->t_unit.size() - G.t_first;
         t->groups.push_back(G);
-        const DevAdj &A = g->adj[G.d];
-        t->hub_need += A.nnz / kHubDeg + 1;
+        const long long nnz = g->adj[G.d].nnz;
+        const long long rows = std::min<long long>(g->n, nnz / kWarpRow + 1);
+        t->row_need += rows;
+        t->chunk_need += nnz / kChunk + rows + 1;
     }
     for (size_t u = 0; u < t->units.size(); u++) {
         QUnit &U = t->units[u];
@@ -1005,6 +1177,36 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
     if ((int)t->t_unit.size() > kMaxTargets || (int)t->u_group.size() > kMaxTargets)
         return fail(RPQ_ERR_INVALID, "automaton has too many transitions");
     return RPQ_OK;
+}
+
+// Appends one JSON line per query: the kernel's phase times and, per level,
+// block 0's timestamps (ns, relative to the kernel start) with the frontier
+// size and the number of push / pull units.
+void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int levels,
+                 cudaStream_t st) {
+    std::vector<unsigned long long> h((size_t)kTraceFields * levels), gs(kTraceFields);
+    if (cudaMemcpyAsync(h.data(), ws->trace.p, h.size() * 8, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(gs.data(),
+                        ws->trace.as<unsigned long long>() + (size_t)kTraceLevels * kTraceFields,
+                        kTraceFields * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    auto rel = [&](unsigned long long t) { return t && gs[0] ? (long long)(t - gs[0]) : -1LL; };
+    fprintf(f, "{\"source\": %d, \"states\": %d, \"kernel\": [%lld, %lld, %lld, %lld], \"levels\": [",
+            source, S, rel(gs[0]), rel(gs[1]), rel(gs[2]), rel(gs[3]));
+    for (int j = 0; j < levels; j++) {
+        const unsigned long long *r = &h[(size_t)j * kTraceFields];
+        if (r[0] == 0) break;
+        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu]", j ? ", " : "", rel(r[0]), rel(r[1]),
+                rel(r[2]), r[3], r[4], r[5]);
+    }
+    fprintf(f, "]}\n");
+    fclose(f);
 }
 
 float env_float(const char *name, float dflt) {
@@ -1028,10 +1230,7 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
     Tables t;
     rpq_status s = build_tables(g, a, &t);
     if (s != RPQ_OK) return s;
-    const size_t tbytes = sizeof(QGroup) * t.groups.size() + sizeof(QUnit) * t.units.size() +
-                          sizeof(int32_t) * (t.t_unit.size() * 2 + t.u_group.size()) + 64;
-    if (tbytes > kTablesBytes) return fail(RPQ_ERR_INVALID, "automaton tables too large");
-    std::unique_ptr<QueryWorkspace> ws = ws_acquire(g, a.S, t.hub_need, &s);
+    std::unique_ptr<QueryWorkspace> ws = ws_acquire(g, a.S, t.row_need, t.chunk_need, &s);
     if (!ws) return s;
     // upload tables
     uint8_t *hs = static_cast<uint8_t *>(ws->staging);
@@ -1039,7 +1238,7 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
     auto put = [&](const void *src, size_t bytes) {
         off = (off + 15) & ~size_t(15);
         size_t at = off;
-        if (bytes) memcpy(hs + at, src, bytes);
+        if (bytes && src && at + bytes <= kTablesBytes) memcpy(hs + at, src, bytes);
         off += bytes;
         return at;
     };
@@ -1049,7 +1248,12 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
     const size_t o_ts = put(t.t_state.data(), sizeof(int32_t) * t.t_state.size());
     const size_t o_ug = put(t.u_group.data(), sizeof(int32_t) * t.u_group.size());
     off = (off + 15) & ~size_t(15);
-    RPQ_CUDA_TRY(cudaMemcpyAsync(ws->tables.p, hs, std::max<size_t>(off, 16), cudaMemcpyHostToDevice, st));
+    if (off > kTablesBytes) {
+        ws_release(g, std::move(ws));
+        return fail(RPQ_ERR_INVALID, "automaton tables too large");
+    }
+    RPQ_CUDA_TRY(cudaMemcpyAsync(ws->tables.p, hs, std::max<size_t>(off, 16),
+                                 cudaMemcpyHostToDevice, st));
     uint8_t *dt = ws->tables.as<uint8_t>();
 
     KParams p{};
@@ -1060,6 +1264,7 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
     p.n_groups = (int32_t)t.groups.size();
     p.n_units = (int32_t)t.units.size();
     p.n_targets = (int32_t)t.t_unit.size();
+    p.n_ugroups = (int32_t)t.u_group.size();
     p.source = source;
     p.max_levels = max_levels;
     p.start_mask = a.start_mask;
@@ -1072,21 +1277,29 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
     p.t_state = reinterpret_cast<const int32_t *>(dt + o_ts);
     p.u_group = reinterpret_cast<const int32_t *>(dt + o_ug);
     p.P = ws->P.as<uint64_t>();
-    p.NX = ws->NX.as<uint64_t>();
-    p.F0 = ws->F0.as<uint64_t>();
-    p.F1 = ws->F1.as<uint64_t>();
-    p.T0 = ws->T0.as<uint32_t>();
-    p.T1 = ws->T1.as<uint32_t>();
-    p.T2 = ws->T2.as<uint32_t>();
-    p.FL0 = ws->FL0.as<int32_t>();
-    p.FL1 = ws->FL1.as<int32_t>();
-    p.H0 = ws->H0.as<Hub>();
-    p.H1 = ws->H1.as<Hub>();
-    p.hub_cap = ws->hub_cap;
+    for (int k = 0; k < 3; k++) {
+        p.F[k] = ws->F[k].as<uint64_t>();
+        p.FL[k] = ws->FL[k].as<int32_t>();
+        p.rows[k] = ws->rows[k].as<Row>();
+        p.cmap[k] = ws->cmap[k].as<int32_t>();
+    }
+    p.row_cap = ws->row_cap;
+    p.chunk_cap = ws->chunk_cap;
     p.mf = ws->mf.as<unsigned long long>();
     p.fin_sums = ws->fin.as<long long>();
     p.c = ws->ctr.as<Counters>();
     p.out_bits = out_bits_dev;
+    static const char *trace_path = getenv("RPQ_TRACE_FILE");
+    if (trace_path) {
+        if (!ws->trace.p &&
+            !ws->trace.alloc(sizeof(unsigned long long) * kTraceFields * (kTraceLevels + 1))) {
+            ws_release(g, std::move(ws));
+            return fail(RPQ_ERR_OOM, "trace buffer");
+        }
+        RPQ_CUDA_TRY(cudaMemsetAsync(ws->trace.p, 0, ws->trace.bytes, st));
+        p.trace = ws->trace.as<unsigned long long>();
+        p.trace_cap = kTraceLevels;
+    }
     if (out_list_dev) {
         p.out_list = out_list_dev;
         p.capacity = capacity;
@@ -1097,9 +1310,9 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
         p.out_list = nullptr;
         p.capacity = 0;
     }
-    const size_t smem = shared_bytes(kMaxGroups, kMaxUnits);
+    const size_t smem = shared_bytes(p.n_groups, p.n_units, p.n_targets, p.n_ugroups);
     int grid = 0;
-    s = get_launch_shape(g->device, &grid);
+    s = get_launch_shape(g->device, smem, &grid);
     if (s != RPQ_OK) {
         ws_release(g, std::move(ws));
         return s;
@@ -1116,8 +1329,6 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
     RPQ_CUDA_TRY(cudaMemcpyAsync(hc, ws->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));
     if (hc->status != 0) {
-        // a failed traversal may leave NX dirty: restore the all-zero invariant
-        cudaMemsetAsync(ws->NX.p, 0, ws->NX.bytes, st);
         cudaMemsetAsync(ws->ctr.p, 0, sizeof(Counters), st);
         cudaStreamSynchronize(st);
         const rpq_status e = (rpq_status)hc->status;
@@ -1146,6 +1357,9 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
                                      cudaMemcpyDeviceToHost, st));
         RPQ_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    if (trace_path)
+        write_trace(trace_path, ws.get(), a.S, source,
+                    (int)std::min<long long>(hc->levels + 2, kTraceLevels), st);
     ws_release(g, std::move(ws));
     return RPQ_OK;
 }

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "rpq.h"
 
 namespace rpq {
@@ -57,6 +59,14 @@ struct Automaton {
 rpq_status compile_regex(const char *text, int32_t n_labels, Automaton *out);
 bool automaton_accepts(const Automaton &a, const int32_t *word, int32_t len);
 Automaton automaton_reverse(const Automaton &a);
+
+bool is_device_pointer(const void *p);
+
+// Exclusive scan of n values into out (int64); the sum goes to *total_dev
+// (device pointer).  Synchronises the stream before returning.
+template <class T>
+rpq_status device_exclusive_scan(const T *in, int64_t *out, int64_t n, int64_t *total_dev,
+                                 cudaStream_t st);
 
 // Single query (query.cu).  See run_query there for the output contract.
 rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,

@@ -3,11 +3,6 @@
 
 using namespace rpq;
 
-extern "C" rpq_status rpq_query_batch(const rpq_graph *, int32_t, const rpq_nfa *const *,
-                                      const int32_t *, int32_t, int64_t *, int32_t *, int64_t,
-                                      rpq_stats *, void *) {
-    return fail(RPQ_ERR_INVALID, "rpq_query_batch is not available in this build");
-}
 extern "C" rpq_status rpq_serve_create(const rpq_graph *, const rpq_serve_config *, rpq_server **) {
     return fail(RPQ_ERR_INVALID, "serving is not available in this build");
 }
