@@ -99,7 +99,7 @@ __device__ bool lane_aggregate(const LParams &p, const LDir &dir, const uint64_t
             const LSrc &S = p.srcs[U.src_first + s];
             x |= sm_M[S.k * kLW + lw] & S.mask[lw];
         }
-        x &= p.active[lw];
+        x &= p.dyn->active[lw];
         sm_X[idx] = x;
         any = any || x != 0;
     }
@@ -165,7 +165,8 @@ __device__ void lane_expand_vertices(const LParams &p, int j, uint64_t *sm_M, ui
         if (i >= nA) break;
         const int32_t v = __ldcg(A + i);
         lane_load_row(p, M, v, sm_M);
-        for (int D = 0; D < p.n_dirs; D++) {
+        const int n_dirs = p.dyn->n_dirs;
+        for (int D = 0; D < n_dirs; D++) {
             const LDir dir = p.dirs[D];
             if (!lane_aggregate(p, dir, sm_M, sm_X)) continue;
             int32_t b, e;
@@ -311,9 +312,26 @@ __global__ void __launch_bounds__(kLThreads) lane_batch_kernel(LParams p, int32_
 
 // -------------------------------------------------------- extraction -----
 // A32[lane][v / 32] = bits of vertices v..v+31 answering lane `lane`.
-__global__ void lane_extract_kernel(const uint64_t *__restrict__ P, int32_t n, int32_t K,
-                                    const uint64_t *__restrict__ fmask, int32_t n_lanes,
-                                    uint32_t *__restrict__ A32, int64_t words32) {
+// For 32 vertices per warp: R[v] = OR_k P[v][k] & fmask[k] per lane word,
+// then one ballot per set lane gives A32[row(lane)][v / 32].  Lanes with
+// row(lane) < 0 are not extracted.  When `clear` is set, the bits of the
+// extracted lanes are also removed from P and from the frontier rows M
+// (their slots are being recycled).
+__global__ void lane_extract_kernel(uint64_t *__restrict__ P, uint64_t *__restrict__ M, int32_t n,
+                                    int32_t K, const uint64_t *__restrict__ fmask,
+                                    const int32_t *__restrict__ lane_row, uint32_t *__restrict__ A32,
+                                    int64_t words32, int clear) {
+    __shared__ int32_t srow[kLanes];
+    __shared__ uint64_t smask[kLW];
+    for (int i = threadIdx.x; i < kLanes; i += blockDim.x) srow[i] = lane_row[i];
+    __syncthreads();
+    if (threadIdx.x < kLW) {
+        uint64_t m = 0;
+        for (int b = 0; b < 64; b++)
+            if (srow[threadIdx.x * 64 + b] >= 0) m |= 1ull << b;
+        smask[threadIdx.x] = m;
+    }
+    __syncthreads();
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned lane = lane_id();
@@ -324,11 +342,20 @@ __global__ void lane_extract_kernel(const uint64_t *__restrict__ P, int32_t n, i
             const size_t base = (size_t)v * K * kLW;
             for (int k = 0; k < K; k++)
 #pragma unroll
-                for (int lw = 0; lw < kLW; lw++)
-                    r[lw] |= __ldg(P + base + (size_t)k * kLW + lw) & __ldg(fmask + k * kLW + lw);
+                for (int lw = 0; lw < kLW; lw++) {
+                    const size_t idx = base + (size_t)k * kLW + lw;
+                    const uint64_t pv = P[idx];
+                    r[lw] |= pv & __ldg(fmask + k * kLW + lw);
+                    if (clear && (pv & smask[lw])) P[idx] = pv & ~smask[lw];
+                    if (clear) {
+                        const uint64_t mv = M[idx];
+                        if (mv & smask[lw]) M[idx] = mv & ~smask[lw];
+                    }
+                }
         }
 #pragma unroll
         for (int lw = 0; lw < kLW; lw++) {
+            r[lw] &= smask[lw];
             const uint32_t lo = __reduce_or_sync(kFull, (uint32_t)r[lw]);
             const uint32_t hi = __reduce_or_sync(kFull, (uint32_t)(r[lw] >> 32));
             uint64_t any = ((uint64_t)hi << 32) | lo;
@@ -336,8 +363,8 @@ __global__ void lane_extract_kernel(const uint64_t *__restrict__ P, int32_t n, i
                 const int b = __ffsll((long long)any) - 1;
                 any &= any - 1;
                 const unsigned bits = __ballot_sync(kFull, (r[lw] >> b) & 1ull);
-                const int ln = lw * 64 + b;
-                if (lane == 0 && ln < n_lanes) A32[(size_t)ln * words32 + chunk] = bits;
+                const int row = srow[lw * 64 + b];
+                if (lane == 0) A32[(size_t)row * words32 + chunk] = bits;
             }
         }
     }
@@ -420,6 +447,60 @@ __global__ void lane_seed_kernel(const int32_t *__restrict__ seeds, int n_seeds,
         const size_t idx = ((size_t)s[0] * K + s[1]) * kLW + s[2];
         atomicOr((unsigned long long *)(M + idx), (unsigned long long)m);
         atomicOr((unsigned long long *)(P + idx), (unsigned long long)m);
+    }
+}
+
+// ---- one level step as separate kernels (server: captured in a graph) ----
+__global__ void __launch_bounds__(kLThreads) lane_step_vertices_kernel(LParams p) {
+    extern __shared__ __align__(16) uint64_t lsm[];
+    const int warp = threadIdx.x >> 5;
+    uint64_t *sm_M = lsm + (size_t)warp * 2 * p.K * kLW;
+    uint64_t *sm_X = sm_M + p.K * kLW;
+    const int j = *(volatile int32_t *)&p.c->step;
+    lane_expand_vertices(p, j, sm_M, sm_X);
+}
+
+__global__ void __launch_bounds__(kLThreads) lane_step_hubs_kernel(LParams p) {
+    extern __shared__ __align__(16) uint64_t lsm[];
+    const int warp = threadIdx.x >> 5;
+    uint64_t *sm_M = lsm + (size_t)warp * 2 * p.K * kLW;
+    uint64_t *sm_X = sm_M + p.K * kLW;
+    const int j = *(volatile int32_t *)&p.c->step;
+    lane_expand_hubs(p, j, sm_M, sm_X);
+}
+
+__global__ void __launch_bounds__(kLThreads) lane_step_commit_kernel(LParams p) {
+    const int j = *(volatile int32_t *)&p.c->step;
+    lane_commit(p, j);
+}
+
+__global__ void lane_step_finish_kernel(LParams p, LaneStepOut *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = p.c->step;
+    out->next_count = p.c->list_count[(j + 1) % 3];
+    for (int lw = 0; lw < kLW; lw++) out->lane_new[lw] = p.c->lane_new[(j + 1) % 3][lw];
+    out->status = p.c->status;
+    lane_reset_for_next(p, j);
+    p.c->step = j + 1;
+    out->step = j + 1;
+}
+
+// Seeds (v, k, lane word, mask lo, mask hi) into frontier M_step and P, and
+// appends vertices to the frontier list of the current step.
+__global__ void lane_seed_step_kernel(LParams p, const int32_t *__restrict__ seeds, int n_seeds,
+                                      const int32_t *__restrict__ verts, int n_verts, int step) {
+    uint64_t *M = (step & 1) ? p.M1 : p.M0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_seeds; i += gridDim.x * blockDim.x) {
+        const int32_t *s = seeds + 5 * i;
+        const uint64_t m = (uint64_t)(uint32_t)s[3] | ((uint64_t)(uint32_t)s[4] << 32);
+        const size_t idx = ((size_t)s[0] * p.K + s[1]) * kLW + s[2];
+        atomicOr((unsigned long long *)(M + idx), (unsigned long long)m);
+        atomicOr((unsigned long long *)(p.P + idx), (unsigned long long)m);
+    }
+    int32_t *A = lane_list(p, step % 3);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_verts; i += gridDim.x * blockDim.x) {
+        const unsigned long long pos = atomicAdd(&p.c->list_count[step % 3], 1ull);
+        A[pos] = verts[i];
     }
 }
 
@@ -508,6 +589,7 @@ rpq_status lane_ws_alloc(LaneWorkspace *ws, const rpq_graph *g, int K) {
     const size_t words = (size_t)g->n * K * kLW;
     const size_t tvw = ((size_t)g->n + 63) / 64;
     const int64_t words32 = ((int64_t)g->n + 31) / 32;
+    const size_t list_cap = (size_t)g->n + 2 * kLanes;  // distinct vertices + seeds of one step
     long long hub_cap = 1024;
     for (int d = 0; d < 2 * g->L; d++) hub_cap += g->adj[d].nnz / kLaneHub + 1;
     ws->n = g->n;
@@ -515,8 +597,8 @@ rpq_status lane_ws_alloc(LaneWorkspace *ws, const rpq_graph *g, int K) {
     ws->hub_cap = hub_cap;
     const int64_t chunks = (words32 + kCountChunk - 1) / kCountChunk;
     if (!ws->M0.alloc(words * 8) || !ws->M1.alloc(words * 8) || !ws->P.alloc(words * 8) ||
-        !ws->NX.alloc(words * 8) || !ws->tv.alloc(tvw * 8) || !ws->l0.alloc(4 * (size_t)g->n) ||
-        !ws->l1.alloc(4 * (size_t)g->n) || !ws->l2.alloc(4 * (size_t)g->n) ||
+        !ws->NX.alloc(words * 8) || !ws->tv.alloc(tvw * 8) || !ws->l0.alloc(4 * list_cap) ||
+        !ws->l1.alloc(4 * list_cap) || !ws->l2.alloc(4 * list_cap) ||
         !ws->hubs.alloc(sizeof(LHub) * hub_cap) || !ws->ctr.alloc(sizeof(LaneCounters)) ||
         !ws->tables.alloc(1 << 20) || !ws->A32.alloc((size_t)kLanes * words32 * 4) ||
         !ws->cnt.alloc(sizeof(int64_t) * (kLanes * chunks + 1)) ||
@@ -525,6 +607,7 @@ rpq_status lane_ws_alloc(LaneWorkspace *ws, const rpq_graph *g, int K) {
     RPQ_CUDA_TRY(cudaMemset(ws->NX.p, 0, words * 8));
     RPQ_CUDA_TRY(cudaMemset(ws->M0.p, 0, words * 8));
     RPQ_CUDA_TRY(cudaMemset(ws->M1.p, 0, words * 8));
+    RPQ_CUDA_TRY(cudaMemset(ws->P.p, 0, words * 8));
     RPQ_CUDA_TRY(cudaMemset(ws->tv.p, 0, tvw * 8));
     RPQ_CUDA_TRY(cudaMemset(ws->ctr.p, 0, sizeof(LaneCounters)));
     ws->staging_bytes = (1 << 20) + 4096;
@@ -558,9 +641,165 @@ void lane_ws_release(rpq_graph *g, std::unique_ptr<LaneWorkspace> w) {
     g->ws_free.emplace_back(std::move(w));
 }
 
+rpq_status lane_ws_acquire_fixed(rpq_graph *g, int K, std::unique_ptr<LaneWorkspace> *out) {
+    rpq_status st = RPQ_OK;
+    *out = lane_ws_acquire(g, K, &st);
+    return *out ? RPQ_OK : st;
+}
+
+void lane_ws_return(rpq_graph *g, std::unique_ptr<LaneWorkspace> w) {
+    lane_ws_release(g, std::move(w));
+}
+
+LParams lane_params(rpq_graph *g, LaneWorkspace *ws, size_t o_dyn, size_t o_dirs, size_t o_units,
+                    size_t o_srcs) {
+    uint8_t *dt = ws->tables.as<uint8_t>();
+    LParams p{};
+    p.adj = g->d_adj.as<DevAdj>();
+    p.n = g->n;
+    p.K = ws->K;
+    p.dyn = reinterpret_cast<const LaneDyn *>(dt + o_dyn);
+    p.dirs = reinterpret_cast<const LDir *>(dt + o_dirs);
+    p.units = reinterpret_cast<const LUnit *>(dt + o_units);
+    p.srcs = reinterpret_cast<const LSrc *>(dt + o_srcs);
+    p.M0 = ws->M0.as<uint64_t>();
+    p.M1 = ws->M1.as<uint64_t>();
+    p.P = ws->P.as<uint64_t>();
+    p.NX = ws->NX.as<uint64_t>();
+    p.tv = ws->tv.as<uint64_t>();
+    p.list0 = ws->l0.as<int32_t>();
+    p.list1 = ws->l1.as<int32_t>();
+    p.list2 = ws->l2.as<int32_t>();
+    p.hubs = ws->hubs.as<LHub>();
+    p.hub_cap = ws->hub_cap;
+    p.c = ws->ctr.as<LaneCounters>();
+    return p;
+}
+
+size_t lane_smem(int K) { return (size_t)kLWarps * 2 * K * kLW * sizeof(uint64_t); }
+
+rpq_status lane_set_smem_limits() {
+    static std::once_flag once;
+    static rpq_status st = RPQ_OK;
+    std::call_once(once, [] {
+        const int mx = (int)lane_smem(kLaneMaxSlots);
+        if (cudaFuncSetAttribute(lane_step_vertices_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+            cudaFuncSetAttribute(lane_step_hubs_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
+            st = fail(RPQ_ERR_CUDA, "lane step kernels: %s", cudaGetErrorString(cudaGetLastError()));
+    });
+    return st;
+}
+
+rpq_status lane_capture_step(const LParams &p, LaneStepOut *out_dev, cudaStream_t st,
+                             cudaGraphExec_t *exec) {
+    rpq_status s = lane_set_smem_limits();
+    if (s != RPQ_OK) return s;
+    int sms = 0;
+    RPQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+    const size_t smem = lane_smem(p.K);
+    cudaGraph_t graph;
+    RPQ_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    lane_step_vertices_kernel<<<sms * 4, kLThreads, smem, st>>>(p);
+    lane_step_hubs_kernel<<<sms * 4, kLThreads, smem, st>>>(p);
+    lane_step_commit_kernel<<<sms * 8, kLThreads, 0, st>>>(p);
+    lane_step_finish_kernel<<<1, 32, 0, st>>>(p, out_dev);
+    RPQ_CUDA_TRY(cudaStreamEndCapture(st, &graph));
+    cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(RPQ_ERR_CUDA, "step graph: %s", cudaGetErrorString(e));
+    return RPQ_OK;
+}
+
+rpq_status lane_seed(const LParams &p, const int32_t *seeds_dev, int n_seeds,
+                     const int32_t *verts_dev, int n_verts, int step, cudaStream_t st) {
+    if (n_seeds == 0 && n_verts == 0) return RPQ_OK;
+    lane_seed_step_kernel<<<1, 256, 0, st>>>(p, seeds_dev, n_seeds, verts_dev, n_verts, step);
+    RPQ_CUDA_TRY(cudaGetLastError());
+    return RPQ_OK;
+}
+
+// Answers of `count` lanes: lane_ids_host[i] gets row i of the extraction.
+// Extraction, counting, scan and ordered write; `clear` also recycles the
+// lanes' bits.  Offsets (count + 1) and answers come back to the host, or
+// the answers go to out_dev (capacity entries) when it is given.
+rpq_status lane_harvest_impl(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
+                             const uint64_t *fmask_dev, const int32_t *lane_row_dev,
+                             int count, bool clear, int cur_step,
+                             std::vector<int64_t> *offsets_host,
+                             std::vector<int32_t> *answers_host, int32_t *out_dev,
+                             int64_t capacity, cudaStream_t st) {
+    const int64_t words32 = ((int64_t)g->n + 31) / 32;
+    const int64_t chunks = (words32 + kCountChunk - 1) / kCountChunk;
+    if (count > 0) RPQ_CUDA_TRY(cudaMemsetAsync(ws->A32.p, 0, (size_t)count * words32 * 4, st));
+    uint64_t *Mcur = (cur_step & 1) ? p.M1 : p.M0;
+    lane_extract_kernel<<<152 * 8, 256, 0, st>>>(p.P, Mcur, g->n, p.K, fmask_dev, lane_row_dev,
+                                                 ws->A32.as<uint32_t>(), words32, clear ? 1 : 0);
+    RPQ_CUDA_TRY(cudaGetLastError());
+    offsets_host->assign((size_t)count + 1, 0);
+    if (count == 0) return RPQ_OK;
+    const long long nblk = (long long)count * chunks;
+    lane_count_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count,
+                                                     chunks, ws->cnt.as<int64_t>());
+    RPQ_CUDA_TRY(cudaGetLastError());
+    rpq_status s = device_exclusive_scan<int64_t>(ws->cnt.as<int64_t>(), ws->pos.as<int64_t>(),
+                                                  nblk, ws->pos.as<int64_t>() + nblk, st);
+    if (s != RPQ_OK) return s;
+    std::vector<int64_t> hpos((size_t)nblk + 1);
+    RPQ_CUDA_TRY(cudaMemcpyAsync(hpos.data(), ws->pos.p, sizeof(int64_t) * (nblk + 1),
+                                 cudaMemcpyDeviceToHost, st));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < count; i++) (*offsets_host)[i] = hpos[(size_t)i * chunks];
+    (*offsets_host)[count] = hpos[nblk];
+    const int64_t total = hpos[nblk];
+    if (total == 0) return RPQ_OK;
+    if (out_dev) {
+        if (total <= capacity) {
+            lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count,
+                                                               chunks, ws->pos.as<int64_t>(), out_dev,
+                                                               capacity);
+            RPQ_CUDA_TRY(cudaGetLastError());
+        }
+        return RPQ_OK;
+    }
+    DevBuf tmp;
+    if (!tmp.alloc(sizeof(int32_t) * total)) return fail(RPQ_ERR_OOM, "answer staging");
+    lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count, chunks,
+                                                       ws->pos.as<int64_t>(), tmp.as<int32_t>(),
+                                                       total);
+    RPQ_CUDA_TRY(cudaGetLastError());
+    answers_host->resize((size_t)total);
+    RPQ_CUDA_TRY(cudaMemcpyAsync(answers_host->data(), tmp.p, sizeof(int32_t) * total,
+                                 cudaMemcpyDeviceToHost, st));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    return RPQ_OK;
+}
+
+rpq_status lane_harvest(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
+                        const uint64_t *fmask_dev, const int32_t *lane_ids_host, int count,
+                        std::vector<int64_t> *offsets_host, std::vector<int32_t> *answers_host,
+                        cudaStream_t st) {
+    // lane -> row map in the staging tail, uploaded to the end of the tables buffer
+    std::vector<int32_t> row(kLanes, -1);
+    for (int i = 0; i < count; i++) row[lane_ids_host[i]] = i;
+    int32_t *hrow = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ws->staging) +
+                                                ws->staging_bytes - 4096 + 2048);
+    memcpy(hrow, row.data(), sizeof(int32_t) * kLanes);
+    int32_t *drow = reinterpret_cast<int32_t *>(ws->tables.as<uint8_t>() + (1 << 20) - 2048);
+    RPQ_CUDA_TRY(cudaMemcpyAsync(drow, hrow, sizeof(int32_t) * kLanes, cudaMemcpyHostToDevice, st));
+    int cur = 0;
+    LaneCounters hc;
+    RPQ_CUDA_TRY(cudaMemcpyAsync(&hc, ws->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    cur = hc.step;
+    return lane_harvest_impl(g, ws, p, fmask_dev, drow, count, true, cur, offsets_host,
+                             answers_host, nullptr, 0, st);
+}
+
 // Runs one lane group (<= 256 queries) to completion and writes the answers.
-// out (host or device per out_is_dev), capacity entries starting at
-// out_base; offsets[i] (group-relative) for i in [0, count].
+// out (host or device per out_is_dev), capacity entries; offsets[i]
+// (group-relative) for i in [0, count].
 rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int32_t *sources,
                           int count, int32_t max_levels, int32_t *out, bool out_is_dev,
                           int64_t capacity, int64_t *offsets, int32_t *lane_levels, float *ms,
@@ -581,41 +820,44 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     std::unique_ptr<LaneWorkspace> ws = lane_ws_acquire(g, K, &as);
     if (!ws) return as;
     K = ws->K;  // slots beyond the automata's states stay empty
-    // re-layout masks for the workspace's K
     fmask.resize((size_t)K * kLW, 0);
-    // seeds: (v, k, lw, mask)
     std::map<std::tuple<int, int, int>, uint64_t> seedm;
     for (int i = 0; i < count; i++) {
         const uint64_t sm = autos[i]->start_mask;
         for (int q = 0; q < autos[i]->S; q++)
             if ((sm >> q) & 1) seedm[std::make_tuple(sources[i], q, i / 64)] |= 1ull << (i % 64);
     }
-    std::vector<int32_t> seeds;
-    std::vector<int32_t> frontier;
+    std::vector<int32_t> seeds, frontier;
     for (auto &kv : seedm) {
         seeds.push_back(std::get<0>(kv.first));
         seeds.push_back(std::get<1>(kv.first));
         seeds.push_back(std::get<2>(kv.first));
         seeds.push_back((int32_t)(uint32_t)kv.second);
         seeds.push_back((int32_t)(uint32_t)(kv.second >> 32));
-        if (frontier.empty() || frontier.back() != std::get<0>(kv.first))
-            frontier.push_back(std::get<0>(kv.first));
+        frontier.push_back(std::get<0>(kv.first));
     }
     std::sort(frontier.begin(), frontier.end());
     frontier.erase(std::unique(frontier.begin(), frontier.end()), frontier.end());
-    // staging: dirs | units | srcs | fmask | seeds | frontier
+    LaneDyn dyn{};
+    dyn.n_dirs = (int32_t)dirs.size();
+    for (int lw = 0; lw < kLW; lw++) {
+        const int lo = lw * 64, hi = std::min(count, lo + 64);
+        dyn.active[lw] = hi <= lo ? 0ull : (hi - lo == 64 ? ~0ull : ((1ull << (hi - lo)) - 1));
+    }
     uint8_t *hs = static_cast<uint8_t *>(ws->staging);
     size_t off = 0;
+    const size_t limit = (1 << 20) - 4096;
     auto put = [&](const void *p, size_t bytes) {
         off = (off + 15) & ~size_t(15);
         const size_t at = off;
-        if (bytes && at + bytes <= ws->staging_bytes) {
+        if (bytes && at + bytes <= limit) {
             if (p) memcpy(hs + at, p, bytes);
             else memset(hs + at, 0, bytes);
         }
         off += bytes;
         return at;
     };
+    const size_t o_dyn = put(&dyn, sizeof(dyn));
     const size_t o_dirs = put(dirs.data(), sizeof(LDir) * dirs.size());
     const size_t o_units = put(units.data(), sizeof(LUnit) * units.size());
     const size_t o_srcs = put(srcs.data(), sizeof(LSrc) * srcs.size());
@@ -623,8 +865,11 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     const size_t o_seed = put(seeds.data(), sizeof(int32_t) * seeds.size());
     const size_t o_front = put(frontier.data(), sizeof(int32_t) * frontier.size());
     const size_t o_last = put(nullptr, sizeof(int32_t) * kLanes);
+    std::vector<int32_t> row(kLanes, -1);
+    for (int i = 0; i < count; i++) row[i] = i;
+    const size_t o_row = put(row.data(), sizeof(int32_t) * kLanes);
     off = (off + 15) & ~size_t(15);
-    if (off + sizeof(LaneCounters) + 64 > ws->staging_bytes) {
+    if (off > limit) {
         lane_ws_release(g, std::move(ws));
         return fail(RPQ_ERR_INVALID, "lane tables too large");
     }
@@ -633,44 +878,13 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     const size_t words = (size_t)g->n * K * kLW;
     RPQ_CUDA_TRY(cudaMemsetAsync(ws->P.p, 0, words * 8, st));
     RPQ_CUDA_TRY(cudaMemsetAsync(ws->ctr.p, 0, sizeof(LaneCounters), st));
-    if (!seeds.empty()) {
-        lane_seed_kernel<<<1, 256, 0, st>>>(reinterpret_cast<const int32_t *>(dt + o_seed),
-                                            (int)(seeds.size() / 5), K, ws->M0.as<uint64_t>(),
-                                            ws->P.as<uint64_t>());
-        RPQ_CUDA_TRY(cudaGetLastError());
-    }
-    RPQ_CUDA_TRY(cudaMemcpyAsync(ws->l0.p, dt + o_front, sizeof(int32_t) * frontier.size(),
-                                 cudaMemcpyDeviceToDevice, st));
-    const unsigned long long nf = frontier.size();
-    RPQ_CUDA_TRY(cudaMemcpyAsync(&ws->ctr.as<LaneCounters>()->list_count[0], &nf, sizeof(nf),
-                                 cudaMemcpyHostToDevice, st));
-
-    LParams p{};
-    p.adj = g->d_adj.as<DevAdj>();
-    p.n = g->n;
-    p.K = K;
-    p.n_dirs = (int32_t)dirs.size();
-    p.dirs = reinterpret_cast<const LDir *>(dt + o_dirs);
-    p.units = reinterpret_cast<const LUnit *>(dt + o_units);
-    p.srcs = reinterpret_cast<const LSrc *>(dt + o_srcs);
-    p.M0 = ws->M0.as<uint64_t>();
-    p.M1 = ws->M1.as<uint64_t>();
-    p.P = ws->P.as<uint64_t>();
-    p.NX = ws->NX.as<uint64_t>();
-    p.tv = ws->tv.as<uint64_t>();
-    p.list0 = ws->l0.as<int32_t>();
-    p.list1 = ws->l1.as<int32_t>();
-    p.list2 = ws->l2.as<int32_t>();
-    p.hubs = ws->hubs.as<LHub>();
-    p.hub_cap = ws->hub_cap;
-    p.c = ws->ctr.as<LaneCounters>();
-    for (int lw = 0; lw < kLW; lw++) {
-        const int lo = lw * 64, hi = std::min(count, lo + 64);
-        p.active[lw] = hi <= lo ? 0ull : (hi - lo == 64 ? ~0ull : ((1ull << (hi - lo)) - 1));
-    }
+    LParams p = lane_params(g, ws.get(), o_dyn, o_dirs, o_units, o_srcs);
+    s = lane_seed(p, reinterpret_cast<const int32_t *>(dt + o_seed), (int)(seeds.size() / 5),
+                  reinterpret_cast<const int32_t *>(dt + o_front), (int)frontier.size(), 0, st);
+    if (s != RPQ_OK) return s;
     int32_t *lane_last = reinterpret_cast<int32_t *>(dt + o_last);
     int grid = 0;
-    const size_t smem = (size_t)kLWarps * 2 * K * kLW * sizeof(uint64_t);
+    const size_t smem = lane_smem(K);
     s = lane_grid(g->device, smem, &grid);
     if (s != RPQ_OK) {
         lane_ws_release(g, std::move(ws));
@@ -690,25 +904,6 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
         return fail(RPQ_ERR_CUDA, "lane kernel launch: %s", cudaGetErrorString(le));
     }
     cudaEventRecord(e1, st);
-    // extraction
-    const int64_t words32 = ((int64_t)g->n + 31) / 32;
-    const int64_t chunks = (words32 + kCountChunk - 1) / kCountChunk;
-    RPQ_CUDA_TRY(cudaMemsetAsync(ws->A32.p, 0, (size_t)count * words32 * 4, st));
-    lane_extract_kernel<<<152 * 8, 256, 0, st>>>(ws->P.as<uint64_t>(), g->n, K,
-                                                 reinterpret_cast<const uint64_t *>(dt + o_fm),
-                                                 count, ws->A32.as<uint32_t>(), words32);
-    RPQ_CUDA_TRY(cudaGetLastError());
-    const long long nblk = (long long)count * chunks;
-    lane_count_kernel<<<(unsigned)std::max<long long>(1, nblk), 256, 0, st>>>(
-        ws->A32.as<uint32_t>(), words32, count, chunks, ws->cnt.as<int64_t>());
-    RPQ_CUDA_TRY(cudaGetLastError());
-    s = device_exclusive_scan<int64_t>(ws->cnt.as<int64_t>(), ws->pos.as<int64_t>(), nblk,
-                                       ws->pos.as<int64_t>() + nblk, st);
-    if (s != RPQ_OK) return s;
-    // offsets per lane = pos at (lane, chunk 0); total at the end
-    std::vector<int64_t> hpos((size_t)nblk + 1);
-    RPQ_CUDA_TRY(cudaMemcpyAsync(hpos.data(), ws->pos.p, sizeof(int64_t) * (nblk + 1),
-                                 cudaMemcpyDeviceToHost, st));
     LaneCounters hc;
     RPQ_CUDA_TRY(cudaMemcpyAsync(&hc, ws->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> hl(kLanes);
@@ -729,39 +924,26 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
         lane_ws_release(g, std::move(ws));
         return fail((rpq_status)hc.status, "lane traversal failed (status %d)", hc.status);
     }
-    for (int i = 0; i < count; i++) offsets[i] = hpos[(size_t)i * chunks];
-    offsets[count] = hpos[nblk];
-    for (int i = 0; i < count; i++) lane_levels[i] = hl[i];
-    if (ms) *ms = kms;
-    const int64_t total = hpos[nblk];
-    // the frontier buffers must be all-zero for the next group: the last
-    // level's M rows were cleared by its commit only for listed vertices
-    const int last = hc.step;
-    (void)last;
+    // answers; the frontier buffers are zeroed for the next group (the last
+    // level's frontier rows are not cleared by a commit)
+    std::vector<int64_t> offs;
+    std::vector<int32_t> host_ans;
+    s = lane_harvest_impl(g, ws.get(), p, reinterpret_cast<const uint64_t *>(dt + o_fm),
+                          reinterpret_cast<const int32_t *>(dt + o_row), count, false, hc.step,
+                          &offs, &host_ans, out_is_dev ? out : nullptr, out_is_dev ? capacity : 0,
+                          st);
     RPQ_CUDA_TRY(cudaMemsetAsync(ws->M0.p, 0, words * 8, st));
     RPQ_CUDA_TRY(cudaMemsetAsync(ws->M1.p, 0, words * 8, st));
-    if (total <= capacity && total > 0) {
-        if (out_is_dev) {
-            lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count,
-                                                               chunks, ws->pos.as<int64_t>(), out,
-                                                               capacity);
-            RPQ_CUDA_TRY(cudaGetLastError());
-        } else {
-            DevBuf tmp;
-            if (!tmp.alloc(sizeof(int32_t) * total)) {
-                lane_ws_release(g, std::move(ws));
-                return fail(RPQ_ERR_OOM, "batch output staging");
-            }
-            lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count,
-                                                               chunks, ws->pos.as<int64_t>(),
-                                                               tmp.as<int32_t>(), total);
-            RPQ_CUDA_TRY(cudaGetLastError());
-            RPQ_CUDA_TRY(cudaMemcpyAsync(out, tmp.p, sizeof(int32_t) * total,
-                                         cudaMemcpyDeviceToHost, st));
-            RPQ_CUDA_TRY(cudaStreamSynchronize(st));
-        }
-    }
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (s != RPQ_OK) {
+        lane_ws_release(g, std::move(ws));
+        return s;
+    }
+    for (int i = 0; i <= count; i++) offsets[i] = offs[i];
+    for (int i = 0; i < count; i++) lane_levels[i] = hl[i];
+    if (ms) *ms = kms;
+    const int64_t total = offs[count];
+    if (!out_is_dev && total <= capacity && total > 0) memcpy(out, host_ans.data(), 4 * total);
     lane_ws_release(g, std::move(ws));
     return RPQ_OK;
 }

@@ -4,6 +4,9 @@
 // replay per level step).
 #pragma once
 
+#include <memory>
+#include <vector>
+
 #include "graph.h"
 
 namespace rpq {
@@ -42,14 +45,24 @@ struct LaneCounters {
     unsigned long long edges;                // edges traversed (all levels)
 };
 
-struct LaneTables {
-    int32_t n_dirs, n_units, n_srcs, pad;
+// Per-step values read by the kernels from device memory (so a captured
+// step graph stays valid when lanes join or leave).
+struct LaneDyn {
+    int32_t n_dirs, pad;
+    uint64_t active[kLW];  // lanes allowed to expand
+};
+
+// What the host reads after each level step.
+struct LaneStepOut {
+    unsigned long long next_count;     // vertices in the next frontier list
+    unsigned long long lane_new[kLW];  // lanes that reached new pairs this step
+    int32_t status, step;
 };
 
 struct LParams {
     const DevAdj *adj;
     int32_t n, K;            // vertices, state slots
-    int32_t n_dirs;
+    const LaneDyn *dyn;
     const LDir *dirs;
     const LUnit *units;
     const LSrc *srcs;
@@ -59,7 +72,6 @@ struct LParams {
     LHub *hubs;
     long long hub_cap;
     LaneCounters *c;
-    uint64_t active[kLW];        // lanes allowed to expand this step
 };
 
 // Device workspace of one lane group (sized for n vertices and K slots).
@@ -71,5 +83,30 @@ struct LaneWorkspace : WorkspaceBase {
     size_t staging_bytes = 0;
     ~LaneWorkspace() override;
 };
+
+// ---- lane engine entry points used by the server (lanes.cu) ----
+rpq_status lane_ws_acquire_fixed(rpq_graph *g, int K, std::unique_ptr<LaneWorkspace> *out);
+void lane_ws_return(rpq_graph *g, std::unique_ptr<LaneWorkspace> w);
+rpq_status lane_build_tables(const rpq_graph *g, const Automaton *const *autos, int count, int K,
+                             std::vector<LDir> *dirs, std::vector<LUnit> *units,
+                             std::vector<LSrc> *srcs, std::vector<uint64_t> *fmask,
+                             std::vector<uint64_t> *smask);
+// Parameters of the lane kernels over workspace ws with its tables buffer
+// laid out as [LaneDyn | LDir[] | LUnit[] | LSrc[]] at the given offsets.
+LParams lane_params(rpq_graph *g, LaneWorkspace *ws, size_t o_dyn, size_t o_dirs, size_t o_units,
+                    size_t o_srcs);
+// Captures one level step (expand, hub chunks, commit, finish) as a graph.
+rpq_status lane_capture_step(const LParams &p, LaneStepOut *out_dev, cudaStream_t st,
+                             cudaGraphExec_t *exec);
+// Seeds: records (v, k, lane word, mask lo, mask hi) into the current frontier
+// and the visited set, and appends the vertices to the current frontier list.
+rpq_status lane_seed(const LParams &p, const int32_t *seeds_dev, int n_seeds,
+                     const int32_t *verts_dev, int n_verts, int step, cudaStream_t st);
+// Answers of the lanes in lane_ids (count of them) into out_dev (sorted per
+// lane); offsets_host gets count + 1 entries.  Clears the lanes' bits.
+rpq_status lane_harvest(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
+                        const uint64_t *fmask_dev, const int32_t *lane_ids_host, int count,
+                        std::vector<int64_t> *offsets_host, std::vector<int32_t> *answers_host,
+                        cudaStream_t st);
 
 }  // namespace rpq

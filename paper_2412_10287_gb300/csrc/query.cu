@@ -367,6 +367,100 @@ __device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t 
     if (acc_e) atomicAdd(&L.s_acc[1], acc_e);
 }
 
+// Batched discovery: lanes with found[r] have discovered (q2, w[r]).  Same
+// effect as kR calls of warp_discover, with the round trips of the kR
+// entries overlapped: one list reservation, one set of row-length loads per
+// group, one chunk-list reservation per group.  q2 warp-uniform; all 32
+// lanes must call.
+template <int kB>
+__device__ void warp_discover_batch(const KParams &p, const Shared &sh, const int32_t *gsf,
+                                    const LevelCtx &L, const bool (&found)[kB], int q2,
+                                    const int32_t (&w)[kB]) {
+    unsigned m[kB];
+    int total = 0;
+#pragma unroll
+    for (int r = 0; r < kB; r++) {
+        m[r] = __ballot_sync(kFull, found[r]);
+        total += __popc(m[r]);
+    }
+    if (!total) return;
+    const unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.c->fl_count[L.slot][q2], (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 0);
+    int32_t *lst = L.FL + (size_t)q2 * p.n;
+    uint64_t *Fq = L.F + (size_t)q2 * p.W;
+    unsigned long long run = base;
+#pragma unroll
+    for (int r = 0; r < kB; r++) {
+        if (found[r]) {
+            lst[run + __popc(m[r] & lanemask_lt())] = w[r];
+            atomicOr((unsigned long long *)(Fq + ((uint32_t)w[r] >> 6)), 1ull << (w[r] & 63));
+        }
+        run += __popc(m[r]);
+    }
+    unsigned long long acc_b = 0, acc_e = 0;
+    for (int g = gsf[q2]; g < gsf[q2 + 1]; g++) {
+        const DevAdj A = p.adj[sh.gd[g]];
+        int32_t rb[kB], re[kB];
+#pragma unroll
+        for (int r = 0; r < kB; r++) {
+            rb[r] = re[r] = 0;
+            if (found[r]) adj_row(A, w[r], rb[r], re[r]);
+        }
+        int nch[kB];
+        int my_rows = 0, my_chunks = 0;
+        unsigned long long mass = 0;
+#pragma unroll
+        for (int r = 0; r < kB; r++) {
+            const int32_t deg = re[r] - rb[r];
+            if (found[r]) {
+                mass += (unsigned long long)deg;
+                acc_b += 8ull + 4ull * (unsigned long long)deg;
+                acc_e += (unsigned long long)deg * (unsigned long long)sh.gtpop[g];
+            }
+            nch[r] = (found[r] && deg >= kWarpRow) ? (deg + kChunk - 1) / kChunk : 0;
+            my_rows += nch[r] ? 1 : 0;
+            my_chunks += nch[r];
+        }
+        if (mass) atomicAdd(&sh.s_mf[g], mass);
+        // warp prefix of (rows, chunks)
+        int ir = my_rows, ic = my_chunks;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yr = __shfl_up_sync(kFull, ir, o);
+            const int yc = __shfl_up_sync(kFull, ic, o);
+            if ((int)lane >= o) {
+                ir += yr;
+                ic += yc;
+            }
+        }
+        const int tr = __shfl_sync(kFull, ir, 31), tc = __shfl_sync(kFull, ic, 31);
+        if (!tr) continue;  // warp-uniform
+        unsigned long long old = 0;
+        if (lane == 0)
+            old = atomicAdd(&p.c->rows_packed[L.slot],
+                            ((unsigned long long)tr << 40) | (unsigned long long)tc);
+        old = __shfl_sync(kFull, old, 0);
+        long long ri = (long long)(old >> 40) + (ir - my_rows);
+        long long cb = (long long)(old & ((1ull << 40) - 1)) + (ic - my_chunks);
+#pragma unroll
+        for (int r = 0; r < kB; r++) {
+            if (!nch[r]) continue;
+            if (ri < p.row_cap && cb + nch[r] <= p.chunk_cap) {
+                L.rows[ri] = Row{g, w[r], rb[r], re[r], cb};
+                for (int k = 0; k < nch[r]; k++) L.cmap[cb + k] = (int32_t)ri;
+            } else {
+                atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
+            }
+            ri++;
+            cb += nch[r];
+        }
+    }
+    if (acc_b) atomicAdd(&L.s_acc[0], acc_b);
+    if (acc_e) atomicAdd(&L.s_acc[1], acc_e);
+}
+
 // General relaxation (any number of target states per lane): edge (., w)
 // into every target in tmask.  All 32 lanes must call.
 __device__ void relax_general(const KParams &p, const Shared &sh, const int32_t *gsf,
@@ -429,8 +523,7 @@ __device__ __forceinline__ void relax_batch(const KParams &p, const Shared &sh, 
             act[r] = !(old & bit);
         }
     }
-#pragma unroll
-    for (int r = 0; r < kR; r++) warp_discover(p, sh, gsf, L, act[r], q2, w[r]);
+    warp_discover_batch<kR>(p, sh, gsf, L, act, q2, w);
 }
 
 // ---------------------------------------------------------------- phases -
@@ -483,48 +576,37 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     }
     __syncthreads();
 
-    // (1) chunks of long rows: whole warps, kClaimChunks chunks per claim
+    // (1) chunks of long rows: chunk c goes to CTA c % grid, warp
+    //     (c / grid) % kWarps of it, so consecutive chunks (one long row)
+    //     spread over all SMs; static, no claims
     {
         const unsigned long long packed = *(volatile unsigned long long *)&p.c->rows_packed[cs];
         const long long nchunks = (long long)(packed & ((1ull << 40) - 1));
-        const long long gwarp = (long long)blockIdx.x * kWarps + warp;
-        const long long nwarps = (long long)gridDim.x * kWarps;
         const Row *R = p.rows[cs];
         const int32_t *CM = p.cmap[cs];
-        for (bool first = true; nchunks > 0; first = false) {
-            long long c0;
-            if (first) {
-                c0 = gwarp * kClaimChunks;
-            } else {
-                unsigned long long t = 0;
-                if (lane == 0)
-                    t = atomicAdd(&p.c->claim_chunk[cs], (unsigned long long)kClaimChunks);
-                c0 = nwarps * kClaimChunks + (long long)__shfl_sync(kFull, t, 0);
-            }
-            if (c0 >= nchunks) break;
-            const long long c1 = min(nchunks, c0 + kClaimChunks);
-            for (long long c = c0; c < c1; c++) {
-                const int ri = __ldcg(CM + c);
-                const int g = __ldcg(&R[ri].g);
-                const uint64_t tmv = sh.tpush[g];
-                if (!tmv) continue;  // warp-uniform
-                const int32_t rb = __ldcg(&R[ri].b), re = __ldcg(&R[ri].e);
-                const long long c0r = __ldcg(&R[ri].chunk0);
-                const int32_t b = rb + (int32_t)((c - c0r) * kChunk);
-                const int32_t e = min(re, b + kChunk);
-                const int32_t *nbr = sh.gnbr[g];
-                bool valid[kR];
-                uint64_t tm[kR];
-                int32_t w[kR];
+        const long long stride = (long long)gridDim.x * kWarps;
+        for (long long c = (long long)blockIdx.x + (long long)warp * gridDim.x; c < nchunks;
+             c += stride) {
+            const int ri = __ldcg(CM + c);
+            const int g = __ldcg(&R[ri].g);
+            const uint64_t tmv = sh.tpush[g];
+            if (!tmv) continue;  // warp-uniform
+            const int32_t rb = __ldcg(&R[ri].b), re = __ldcg(&R[ri].e);
+            const long long c0r = __ldcg(&R[ri].chunk0);
+            const int32_t b = rb + (int32_t)((c - c0r) * kChunk);
+            const int32_t e = min(re, b + kChunk);
+            const int32_t *nbr = sh.gnbr[g];
+            bool valid[kR];
+            uint64_t tm[kR];
+            int32_t w[kR];
 #pragma unroll
-                for (int r = 0; r < kR; r++) {
-                    const int32_t k = b + r * 32 + (int32_t)lane;
-                    valid[r] = k < e;
-                    w[r] = valid[r] ? __ldg(nbr + k) : 0;
-                    tm[r] = tmv;
-                }
-                relax_batch(p, sh, gsf, L, valid, tm, w);
+            for (int r = 0; r < kR; r++) {
+                const int32_t k = b + r * 32 + (int32_t)lane;
+                valid[r] = k < e;
+                w[r] = valid[r] ? __ldg(nbr + k) : 0;
+                tm[r] = tmv;
             }
+            relax_batch(p, sh, gsf, L, valid, tm, w);
         }
     }
 
