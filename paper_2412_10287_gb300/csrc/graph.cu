@@ -277,6 +277,29 @@ __global__ void rows_per_label_kernel(const int64_t *rscan, const int32_t *rf, c
     }
 }
 
+// rows of at least `minlen` edges and their chunk count, for one adjacency
+__global__ void long_rows_kernel(DevAdj A, int32_t minlen, int32_t chunk,
+                                 unsigned long long *out /* [2] */) {
+    const int64_t rows = A.fmt == ADJ_EMPTY ? 0 : A.nrows;
+    unsigned long long nr = 0, nc = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t deg = A.off[r + 1] - A.off[r];
+        if (deg >= minlen) {
+            nr++;
+            nc += (unsigned long long)((deg + chunk - 1) / chunk);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        nr += __shfl_down_sync(kFull, nr, o);
+        nc += __shfl_down_sync(kFull, nc, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (nr || nc)) {
+        atomicAdd(out, nr);
+        atomicAdd(out + 1, nc);
+    }
+}
+
 unsigned grid_for(int64_t n, int threads = 256) {
     int64_t b = (n + threads - 1) / threads;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
@@ -523,6 +546,30 @@ extern "C" rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64
         g->m_unique = mu;
         rpq_status s = build_side(g.get(), side == 1, o[1], o[2], nb->as<int32_t>(), mu, st);
         if (s != RPQ_OK) return s;
+    }
+    // long-row statistics per direction
+    {
+        DevBuf lr;
+        const size_t nd = g->adj.size();
+        if (!lr.alloc(sizeof(unsigned long long) * 2 * nd)) return fail(RPQ_ERR_OOM, "row statistics");
+        RPQ_CUDA_TRY(cudaMemsetAsync(lr.p, 0, sizeof(unsigned long long) * 2 * nd, st));
+        for (size_t d = 0; d < nd; d++) {
+            const DevAdj &A = g->adj[d];
+            if (A.fmt == ADJ_EMPTY) continue;
+            long_rows_kernel<<<grid_for(A.nrows), 256, 0, st>>>(
+                A, rpq_graph::kLongRow, rpq_graph::kLongChunk, lr.as<unsigned long long>() + 2 * d);
+            RPQ_CUDA_TRY(cudaGetLastError());
+        }
+        std::vector<unsigned long long> h(2 * nd);
+        RPQ_CUDA_TRY(cudaMemcpyAsync(h.data(), lr.p, sizeof(unsigned long long) * 2 * nd,
+                                     cudaMemcpyDeviceToHost, st));
+        RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+        g->long_rows.assign(nd, 0);
+        g->long_chunks.assign(nd, 0);
+        for (size_t d = 0; d < nd; d++) {
+            g->long_rows[d] = (int64_t)h[2 * d];
+            g->long_chunks[d] = (int64_t)h[2 * d + 1];
+        }
     }
     if (!g->d_adj.alloc(sizeof(DevAdj) * g->adj.size())) return fail(RPQ_ERR_OOM, "adjacency table");
     RPQ_CUDA_TRY(cudaMemcpyAsync(g->d_adj.p, g->adj.data(), sizeof(DevAdj) * g->adj.size(),

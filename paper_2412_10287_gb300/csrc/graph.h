@@ -28,6 +28,11 @@ struct rpq_graph {
     // d >= L -> CSC of G^{d-L} (in-rows), i.e. the out-rows of G^{(d-L)^-}.
     std::vector<rpq::DevAdj> adj;
     std::vector<int64_t> nnz;  // distinct edges per label
+    // per direction d: rows with at least kLongRow edges, and the sum over
+    // them of ceil(deg / kLongChunk) (sizes of the query kernel's row lists)
+    std::vector<int64_t> long_rows, long_chunks;
+    static constexpr int kLongRow = 32;
+    static constexpr int kLongChunk = 128;
     rpq::DevBuf d_adj;         // device copy of adj
     rpq::DevBuf csr_nbr, csc_nbr;  // distinct neighbour ids, label-major
     std::vector<std::unique_ptr<rpq::DevBuf>> owned;  // offsets / hypersparse rows

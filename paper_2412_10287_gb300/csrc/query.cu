@@ -39,8 +39,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kR = 4;                 // edges per lane per round in the batched loops
-constexpr int kWarpRow = 32;          // rows with at least this many edges are chunked
+constexpr int kWarpRow = rpq_graph::kLongRow;  // rows with at least this many edges are chunked
 constexpr int kChunk = 32 * kR;       // edges per chunk: one warp round
+static_assert(kChunk == rpq_graph::kLongChunk, "chunk size must match the graph's row statistics");
 constexpr int kClaimChunks = 4;       // chunks a warp claims at once
 constexpr int kGather = 1024;         // gather buffer entries per CTA
 constexpr int kMaxGroups = 512;
@@ -1242,10 +1243,10 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
         }
         G.t_count = (int32_t)t->t_unit.size() - G.t_first;
         t->groups.push_back(G);
-        const long long nnz = g->adj[G.d].nnz;
-        const long long rows = std::min<long long>(g->n, nnz / kWarpRow + 1);
-        t->row_need += rows;
-        t->chunk_need += nnz / kChunk + rows + 1;
+        // a level holds each (state, vertex) pair at most once, so the long
+        // rows of one group are at most the long rows of its adjacency
+        t->row_need += g->long_rows[G.d] + 1;
+        t->chunk_need += g->long_chunks[G.d] + 1;
     }
     for (size_t u = 0; u < t->units.size(); u++) {
         QUnit &U = t->units[u];
@@ -1447,3 +1448,4 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
 }
 
 }  // namespace rpq
+
