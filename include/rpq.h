@@ -170,6 +170,27 @@ rpq_status rpq_query(const rpq_graph *g, const rpq_nfa *nfa, int32_t source, int
                      int32_t *out_vertices, int64_t capacity, int64_t *out_count,
                      rpq_stats *stats, void *stream);
 
+/* Single-source query that allocates no device memory.  The paper has no
+ * counterpart: this is for callers that must not allocate on the GPU --
+ * code running where every byte of device memory is owned by another
+ * allocator (an inference server's memory pool, a real-time system that
+ * fixes its footprint at start-up) or where an allocation would
+ * synchronise or fail.  The traversal is the same as rpq_query; its
+ * workspace is a fixed 64 MiB array in device memory that the library
+ * reserves on every GPU that loads it, for as long as it stays loaded.
+ *   out_vertices: DEVICE memory, capacity entries (the sorted answer).
+ *   Errors as rpq_query, plus RPQ_ERR_INVALID when out_vertices is not device
+ *   memory, when the graph's device is not the current one, or when the
+ *   query needs more than the 64 MiB of scratch (about S x n x 12.5 bytes
+ *   for an automaton of S states on n vertices; use rpq_query then).
+ * The first call on a device looks up the array's device address and clears
+ * its counters; make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (other threads,
+ * other streams) race and must be serialised by the caller. */
+rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, int32_t source,
+                             int32_t max_levels, int32_t *out_vertices, int64_t capacity,
+                             int64_t *out_count, void *stream);
+
 /* Same query; the answer is written as a bitset of ceil(n/64) uint64 words
  * (bit v of word v/64 set iff v answers).  `out_bits` host or device. */
 rpq_status rpq_query_bitset(const rpq_graph *g, const rpq_nfa *nfa, int32_t source,

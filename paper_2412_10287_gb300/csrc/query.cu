@@ -1449,3 +1449,165 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
 
 }  // namespace rpq
 
+// --------------------------------------------------- no-allocation entry --
+// Scratch for rpq_query_noalloc: a fixed device array that exists for as
+// long as the library is loaded, so a query needs no device allocation.
+#define RPQ_NOALLOC_SCRATCH_BYTES (64ull << 20)
+static __device__ __align__(256) unsigned char rpq_noalloc_scratch[RPQ_NOALLOC_SCRATCH_BYTES];
+
+namespace rpq {
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64];  // device address of the scratch, per device
+
+// Device address of the scratch on `device` (which must be current), looked
+// up once per device; the barrier counters are cleared on that first call.
+rpq_status noalloc_scratch(int device, void **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (device < 0 || device >= 64) return fail(RPQ_ERR_CUDA, "device id %d", device);
+    if (!g_noalloc_ptr[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, rpq_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(RPQ_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        RPQ_CUDA_TRY(cudaMemset(ptr, 0, sizeof(Counters)));
+        g_noalloc_ptr[device] = ptr;
+    }
+    *out = g_noalloc_ptr[device];
+    return RPQ_OK;
+}
+}  // namespace
+}  // namespace rpq
+
+using namespace rpq;
+
+extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, int32_t source,
+                                        int32_t max_levels, int32_t *out_vertices,
+                                        int64_t capacity, int64_t *out_count, void *stream) {
+    clear_error();
+    if (!g || !nfa || !out_count) return fail(RPQ_ERR_INVALID, "null argument");
+    if (capacity < 0 || (capacity > 0 && !out_vertices))
+        return fail(RPQ_ERR_INVALID, "bad output buffer");
+    if (out_vertices && !is_device_pointer(out_vertices))
+        return fail(RPQ_ERR_INVALID, "rpq_query_noalloc writes device memory only");
+    *out_count = 0;
+    const Automaton &a = nfa->a;
+    if (source < 0 || source >= g->n)
+        return fail(RPQ_ERR_INVALID, "source %d outside [0, %d)", source, g->n);
+    if (max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
+    if (a.S <= 0 || a.S > kMaxStates) return fail(RPQ_ERR_INVALID, "automaton has %d states", a.S);
+    int dev = -1;
+    RPQ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != g->device)
+        return fail(RPQ_ERR_INVALID, "make the graph's device (%d) current first", g->device);
+    Tables t;
+    rpq_status s = build_tables(g, a, &t);
+    if (s != RPQ_OK) return s;
+
+    // scratch layout: counters | mf | per-CTA sums | tables | P | F[3] | FL[3] | rows[3] | cmap[3]
+    const int64_t W = ((int64_t)g->n + 63) / 64;
+    std::vector<uint8_t> host_tables;
+    size_t toff = 0;
+    auto put = [&](const void *src, size_t bytes) {
+        toff = (toff + 15) & ~size_t(15);
+        const size_t at = toff;
+        host_tables.resize(toff + bytes);
+        if (bytes) memcpy(host_tables.data() + at, src, bytes);
+        toff += bytes;
+        return at;
+    };
+    const size_t o_groups = put(t.groups.data(), sizeof(QGroup) * t.groups.size());
+    const size_t o_units = put(t.units.data(), sizeof(QUnit) * t.units.size());
+    const size_t o_tu = put(t.t_unit.data(), sizeof(int32_t) * t.t_unit.size());
+    const size_t o_ts = put(t.t_state.data(), sizeof(int32_t) * t.t_state.size());
+    const size_t o_ug = put(t.u_group.data(), sizeof(int32_t) * t.u_group.size());
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        const size_t at = off;
+        off += bytes;
+        return at;
+    };
+    const size_t x_ctr = take(sizeof(Counters));
+    const size_t x_mf = take(sizeof(unsigned long long) * 3 * kMaxGroups);
+    const size_t x_fin = take(sizeof(long long) * 152 * 64);
+    const size_t x_tab = take(std::max<size_t>(toff, 16));
+    const size_t bits = sizeof(uint64_t) * (size_t)a.S * W;
+    const size_t fl = sizeof(int32_t) * (size_t)a.S * g->n;
+    const size_t x_P = take(bits);
+    size_t x_F[3], x_FL[3], x_rows[3], x_cmap[3];
+    for (int k = 0; k < 3; k++) x_F[k] = take(bits);
+    for (int k = 0; k < 3; k++) x_FL[k] = take(fl);
+    for (int k = 0; k < 3; k++) x_rows[k] = take(sizeof(Row) * (size_t)t.row_need);
+    for (int k = 0; k < 3; k++) x_cmap[k] = take(sizeof(int32_t) * (size_t)t.chunk_need);
+    if (off > RPQ_NOALLOC_SCRATCH_BYTES)
+        return fail(RPQ_ERR_INVALID,
+                    "query needs %zu bytes of scratch; rpq_query_noalloc holds %llu "
+                    "(use rpq_query)",
+                    off, (unsigned long long)RPQ_NOALLOC_SCRATCH_BYTES);
+    void *base_v = nullptr;
+    s = noalloc_scratch(dev, &base_v);
+    if (s != RPQ_OK) return s;
+    uint8_t *base = static_cast<uint8_t *>(base_v);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    RPQ_CUDA_TRY(cudaMemcpyAsync(base + x_tab, host_tables.data(), std::max<size_t>(toff, 1),
+                                 cudaMemcpyHostToDevice, st));
+
+    KParams p{};
+    p.adj = g->d_adj.as<DevAdj>();
+    p.n = g->n;
+    p.W = (int32_t)W;
+    p.S = a.S;
+    p.n_groups = (int32_t)t.groups.size();
+    p.n_units = (int32_t)t.units.size();
+    p.n_targets = (int32_t)t.t_unit.size();
+    p.n_ugroups = (int32_t)t.u_group.size();
+    p.source = source;
+    p.max_levels = max_levels;
+    p.start_mask = a.start_mask;
+    p.final_mask = a.final_mask;
+    p.alpha = env_float("RPQ_PULL_ALPHA", 4.0f);
+    p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", 256.0f);
+    p.groups = reinterpret_cast<const QGroup *>(base + x_tab + o_groups);
+    p.units = reinterpret_cast<const QUnit *>(base + x_tab + o_units);
+    p.t_unit = reinterpret_cast<const int32_t *>(base + x_tab + o_tu);
+    p.t_state = reinterpret_cast<const int32_t *>(base + x_tab + o_ts);
+    p.u_group = reinterpret_cast<const int32_t *>(base + x_tab + o_ug);
+    p.P = reinterpret_cast<uint64_t *>(base + x_P);
+    for (int k = 0; k < 3; k++) {
+        p.F[k] = reinterpret_cast<uint64_t *>(base + x_F[k]);
+        p.FL[k] = reinterpret_cast<int32_t *>(base + x_FL[k]);
+        p.rows[k] = reinterpret_cast<Row *>(base + x_rows[k]);
+        p.cmap[k] = reinterpret_cast<int32_t *>(base + x_cmap[k]);
+    }
+    p.row_cap = t.row_need;
+    p.chunk_cap = t.chunk_need;
+    p.mf = reinterpret_cast<unsigned long long *>(base + x_mf);
+    p.fin_sums = reinterpret_cast<long long *>(base + x_fin);
+    p.c = reinterpret_cast<Counters *>(base + x_ctr);
+    p.out_list = out_vertices;
+    p.capacity = out_vertices ? capacity : 0;
+    p.out_bits = nullptr;
+    const size_t smem = shared_bytes(p.n_groups, p.n_units, p.n_targets, p.n_ugroups);
+    int grid = 0;
+    s = get_launch_shape(dev, smem, &grid);
+    if (s != RPQ_OK) return s;
+    RPQ_CUDA_TRY(cudaMemsetAsync(&p.c->status, 0, sizeof(int32_t), st));
+    void *args[] = {&p};
+    RPQ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)rpq_query_kernel, dim3(grid),
+                                             dim3(kThreads), args, smem, st));
+    Counters hc;
+    RPQ_CUDA_TRY(cudaMemcpyAsync(&hc, p.c, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hc.status != 0) {
+        // a traversal that gave up leaves the barrier counters mid-way: reset them
+        cudaMemsetAsync(p.c, 0, sizeof(Counters), st);
+        cudaStreamSynchronize(st);
+        return fail((rpq_status)hc.status, "device traversal failed (status %d)", hc.status);
+    }
+    *out_count = hc.answer_count;
+    if (hc.answer_count > capacity)
+        return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices, capacity %lld",
+                    (long long)hc.answer_count, (long long)capacity);
+    return RPQ_OK;
+}

@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "RPQ_OK", 1: "RPQ_ERR_INVALID", 2: "RPQ_ERR_PARSE", 3: "RPQ_E
 EXPORTED = (
     "rpq_set_allocator", "rpq_graph_load", "rpq_graph_free", "rpq_graph_info", "rpq_graph_export",
     "rpq_nfa_compile", "rpq_nfa_from_transitions", "rpq_nfa_free", "rpq_nfa_info",
-    "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_query_bitset",
+    "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_query_noalloc",
+    "rpq_query_bitset",
     "rpq_query_batch", "rpq_serve_create", "rpq_serve_submit", "rpq_serve_poll",
     "rpq_serve_drain", "rpq_serve_stats_get", "rpq_serve_destroy", "rpq_last_error",
     "rpq_version",
@@ -99,6 +100,7 @@ def lib():
             "rpq_nfa_accepts": [p, p, i32, p],
             "rpq_nfa_reverse": [p, pp],
             "rpq_query": [p, p, i32, i32, p, i64, p, p, p],
+            "rpq_query_noalloc": [p, p, i32, i32, p, i64, p, p],
             "rpq_query_bitset": [p, p, i32, i32, p, p, p, p],
             "rpq_query_batch": [p, i32, p, p, i32, p, p, i64, p, p],
             "rpq_serve_create": [p, p, pp],
@@ -346,6 +348,17 @@ def rpq_query(g: Graph, nfa: Nfa, source: int, max_levels: int = 0, out=None, st
                                ctypes.byref(cnt), sp, _stream_handle(stream)))
         res = int(cnt.value)
     return (res, st.as_dict()) if with_stats else res
+
+
+def rpq_query_noalloc(g: Graph, nfa: Nfa, source: int, out, max_levels: int = 0,
+                      stream=None) -> int:
+    """Single-source query through the entry point that allocates no device
+    memory (its workspace is a fixed array inside the library).  ``out`` is a
+    device int32 tensor; returns the number of answer vertices written."""
+    cnt = ctypes.c_int64()
+    _check(lib().rpq_query_noalloc(g.h, nfa.h, int(source), int(max_levels), _ptr(out),
+                                   out.numel(), ctypes.byref(cnt), _stream_handle(stream)))
+    return int(cnt.value)
 
 
 def rpq_query_bitset(g: Graph, nfa: Nfa, source: int, max_levels: int = 0, out=None,
