@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "batch", "serve"],
+                    help="rmat20: single queries (the default line); batch: 256 mixed queries "
+                         "per launch; serve: Poisson arrivals through the server")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -225,12 +229,173 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ batch / serve ----
+
+def run_batch(args, R, torch):
+    """256 mixed queries (2-12 DFA states) per rpq_query_batch launch against
+    the same 256 queries run one at a time."""
+    from paper_2412_10287_gb300 import workloads as W
+
+    g = W.config2_graph()
+    w = W.config4(g, 256)
+    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
+    srcs = [q.source for q in w.queries]
+    states = [n.info()[0] for n in nfas]
+    res = R.rpq_query_batch(gg, nfas, srcs)  # warm-up, sizes the output
+    total = sum(a.size for a in res)
+    out = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+    offs = np.zeros(len(nfas) + 1, np.int64)
+    import ctypes
+
+    handles = (ctypes.c_void_p * len(nfas))(*[x.h.value for x in nfas])
+    src_arr = np.array(srcs, np.int32)
+    stream = torch.cuda.current_stream()
+
+    def batch_once():
+        s = R.lib().rpq_query_batch(gg.h, len(nfas), handles, R._ptr(src_arr), 0, R._ptr(offs),
+                                    R._ptr(out), out.numel(), None,
+                                    ctypes.c_void_p(stream.cuda_stream))
+        assert s == 0, R.rpq_last_error()
+
+    def seq_once():
+        one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for nfa, s in zip(nfas, srcs):
+            R.rpq_query(gg, nfa, s, out=one, stream=stream)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        batch_once()
+        seq_once()
+    tb, ts = [], []
+    for _ in range(args.steps):
+        for fn, acc in ((batch_once, tb), (seq_once, ts)):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            acc.append(e0.elapsed_time(e1) / 1000.0)
+    qb = len(nfas) * args.steps / sum(tb)
+    qs = len(nfas) * args.steps / sum(ts)
+    line = {"metric": "rpq_queries_per_s", "value": qb, "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(tb) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "rmat20_batch: the rmat20 graph; 256 mixed queries per launch "
+                                   f"(DFA states {min(states)}-{max(states)}) packed as uint64 "
+                                   "bit lanes; seed 3",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "sequential_single_queries_per_s": qs, "batch_speedup": qb / qs,
+            "answer_vertices_per_step": int(total), "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args, R, torch):
+    """Poisson arrivals (2,000 q/s) replayed in real time into the server, and
+    into a one-at-a-time served loop; then both at saturation."""
+    import threading
+
+    from paper_2412_10287_gb300 import workloads as W
+
+    g = W.config2_graph()
+    w = W.config5(g, rate=2000.0, duration_s=args.serve_seconds, warmup_s=1.0)
+    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    nfas = {}
+    for q in w.queries:
+        if q.regex not in nfas:
+            nfas[q.regex] = R.rpq_nfa_compile(q.regex, g.n_labels)
+    qs = w.queries
+    srv = R.Server(gg, max_lanes=256, max_states=16)
+    # warm-up burst
+    for q in qs[:256]:
+        srv.submit(nfas[q.regex], q.source)
+    srv.drain(600000)
+    srv.close()
+
+    def served(server):
+        t0 = time.perf_counter()
+        tickets = []
+        for q in qs:
+            dt = q.arrival_s - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(server.submit(nfas[q.regex], q.source))
+        server.drain(600000)
+        st = server.stats()
+        for t in tickets:
+            server.poll(t)
+        return st
+
+    srv = R.Server(gg, max_lanes=256, max_states=16)
+    st_srv = served(srv)
+    srv.close()
+
+    # unbatched served loop: one query at a time in arrival order
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    lat = []
+    t0 = time.perf_counter()
+    for q in qs:
+        now = time.perf_counter() - t0
+        if q.arrival_s > now:
+            time.sleep(q.arrival_s - now)
+        R.rpq_query(gg, nfas[q.regex], q.source, out=out, stream=stream)
+        lat.append((time.perf_counter() - t0 - q.arrival_s) * 1000.0)
+    span = time.perf_counter() - t0
+    lat.sort()
+    unb = {"qps": len(qs) / span, "p50_ms": lat[len(lat) // 2],
+           "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+    # saturation: everything submitted at once
+    sat_n = min(len(qs), 4096)
+    srv = R.Server(gg, max_lanes=256, max_states=16)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(nfas[q.regex], q.source) for q in qs[:sat_n]]
+    srv.drain(600000)
+    sat_srv = sat_n / (time.perf_counter() - t0)
+    for t in tickets:
+        srv.poll(t)
+    srv.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in qs[:sat_n]:
+        R.rpq_query(gg, nfas[q.regex], q.source, out=out, stream=stream)
+    sat_seq = sat_n / (time.perf_counter() - t0)
+
+    line = {"metric": "rpq_served_queries_per_s", "value": st_srv["qps"], "unit": "queries/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"rmat20_serve: Poisson arrivals at 2,000 q/s for "
+                                   f"{args.serve_seconds + 1.0:.0f} s ({len(qs)} queries, mixed "
+                                   "templates of 1-12 DFA states), 256 lanes x 16 state slots"},
+            "p50_ms": st_srv["p50_ms"], "p99_ms": st_srv["p99_ms"],
+            "level_steps": st_srv["level_steps"],
+            "unbatched_served_loop": unb,
+            "saturation_queries_per_s": {"server": sat_srv, "one_at_a_time": sat_seq,
+                                         "queries": sat_n}}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------- GPU path ---
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "rmat20":
+        import torch
+
+        torch.cuda.set_device(0)
+        import __graft_entry__
+
+        __graft_entry__.build()
+        from paper_2412_10287_gb300 import rpq as R
+
+        (run_batch if args.workload == "batch" else run_serve)(args, R, torch)
         return
     import torch
 

@@ -1,0 +1,506 @@
+// Serving: continuous batching of single-source queries over the lane engine.
+//
+// The paper runs queries one at a time (section 5.3).  A server instead keeps
+// the graph and the state of every admitted query resident on the device and
+// lets queries that arrive while others run join at the next level boundary:
+//
+//   loop
+//     admit    queued queries take free lanes (one bit of the 256-lane vector
+//              per query; automaton state q in slot q); their source is
+//              seeded into the current frontier and the visited set;
+//     step     one level of Algorithm 1 for every lane at once: the captured
+//              CUDA graph of the lane step (expand frontier rows, expand long
+//              row chunks, commit, read back the lanes that found new pairs);
+//     retire   a lane whose frontier is now empty (or that reached the level
+//              cap) is finished: one pass over the visited set extracts the
+//              answers of all finishing lanes and clears their bits, and the
+//              lanes become free.
+//
+// Lanes never interact (every Boolean operation is bitwise per lane), so an
+// answer is the same whether the query ran alone or among others.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "lanes.h"
+
+using Clock = std::chrono::steady_clock;
+
+namespace rpq {
+namespace {
+
+constexpr size_t kServeTablesBytes = 4u << 20;
+
+struct Pending {
+    uint64_t ticket;
+    Automaton a;
+    int32_t source;
+    Clock::time_point t_submit;
+};
+
+struct Done {
+    rpq_status status = RPQ_OK;
+    std::vector<int32_t> answer;
+};
+
+struct Lane {
+    bool busy = false;
+    bool finished = false;
+    uint64_t ticket = 0;
+    Automaton a;
+    int32_t source = 0;
+    int level = 0;
+    Clock::time_point t_submit;
+};
+
+}  // namespace
+}  // namespace rpq
+
+struct rpq_server {
+    rpq_graph *g = nullptr;
+    int lanes_max = 0, K = 0, max_levels = 0;
+    size_t queue_cap = 0;
+    std::unique_ptr<rpq::LaneWorkspace> ws;
+    cudaStream_t st = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    rpq::DevBuf tables, step_out;
+    void *staging = nullptr;            // pinned: tables upload
+    rpq::LaneStepOut *out_host = nullptr;  // pinned: step read-back
+    rpq::LParams p{};
+    size_t o_dyn = 0, o_dirs = 0, o_units = 0, o_srcs = 0, o_fm = 0, o_seed = 0, o_verts = 0;
+
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    std::deque<rpq::Pending> queue;
+    std::unordered_map<uint64_t, rpq::Done> results;
+    std::unordered_map<uint64_t, int> inflight;  // ticket -> 1 (queued or running)
+    rpq::Lane lane[rpq::kLanes];
+    bool stop = false;
+    std::thread worker;
+    uint64_t next_ticket = 1;
+    // statistics
+    int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, level_steps = 0;
+    std::vector<double> latency_ms;
+    bool started = false;
+    Clock::time_point t_first, t_last;
+    rpq_status fatal = RPQ_OK;
+};
+
+namespace rpq {
+namespace {
+
+void lane_masks(const rpq_server *s, uint64_t active[kLW]) {
+    for (int w = 0; w < kLW; w++) active[w] = 0;
+    for (int i = 0; i < kLanes; i++)
+        if (s->lane[i].busy && !s->lane[i].finished) active[i / 64] |= 1ull << (i % 64);
+}
+
+// Rebuilds the lane tables from the current lane -> automaton assignment and
+// uploads them (stream-ordered before the next step).
+rpq_status upload_tables(rpq_server *s) {
+    std::vector<const Automaton *> autos(kLanes, nullptr);
+    for (int i = 0; i < kLanes; i++)
+        if (s->lane[i].busy) autos[i] = &s->lane[i].a;
+    std::vector<LDir> dirs;
+    std::vector<LUnit> units;
+    std::vector<LSrc> srcs;
+    std::vector<uint64_t> fmask, smask;
+    rpq_status st = lane_build_tables(s->g, autos.data(), kLanes, s->K, &dirs, &units, &srcs, &fmask,
+                                      &smask);
+    if (st != RPQ_OK) return st;
+    fmask.resize((size_t)s->ws->K * kLW, 0);
+    LaneDyn dyn{};
+    dyn.n_dirs = (int32_t)dirs.size();
+    lane_masks(s, dyn.active);
+    const size_t need_dirs = sizeof(LDir) * dirs.size(), need_units = sizeof(LUnit) * units.size(),
+                 need_srcs = sizeof(LSrc) * srcs.size();
+    if (need_dirs > s->o_units - s->o_dirs || need_units > s->o_srcs - s->o_units ||
+        need_srcs > s->o_fm - s->o_srcs)
+        return fail(RPQ_ERR_INVALID, "lane tables exceed the server's table space");
+    uint8_t *hs = static_cast<uint8_t *>(s->staging);
+    memcpy(hs + s->o_dyn, &dyn, sizeof(dyn));
+    if (need_dirs) memcpy(hs + s->o_dirs, dirs.data(), need_dirs);
+    if (need_units) memcpy(hs + s->o_units, units.data(), need_units);
+    if (need_srcs) memcpy(hs + s->o_srcs, srcs.data(), need_srcs);
+    memcpy(hs + s->o_fm, fmask.data(), sizeof(uint64_t) * fmask.size());
+    uint8_t *dt = s->tables.as<uint8_t>();
+    auto up = [&](size_t at, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dt + at, hs + at, bytes, cudaMemcpyHostToDevice, s->st)
+                     : cudaSuccess;
+    };
+    RPQ_CUDA_TRY(up(s->o_dyn, sizeof(dyn)));
+    RPQ_CUDA_TRY(up(s->o_dirs, need_dirs));
+    RPQ_CUDA_TRY(up(s->o_units, need_units));
+    RPQ_CUDA_TRY(up(s->o_srcs, need_srcs));
+    RPQ_CUDA_TRY(up(s->o_fm, sizeof(uint64_t) * fmask.size()));
+    return RPQ_OK;
+}
+
+void finish_ticket(rpq_server *s, uint64_t ticket, rpq_status status, std::vector<int32_t> ans,
+                   Clock::time_point t_submit) {
+    // caller holds s->mu
+    Done d;
+    d.status = status;
+    d.answer = std::move(ans);
+    s->results[ticket] = std::move(d);
+    s->inflight.erase(ticket);
+    s->completed++;
+    const auto now = Clock::now();
+    s->t_last = now;
+    s->latency_ms.push_back(std::chrono::duration<double, std::milli>(now - t_submit).count());
+}
+
+void worker_main(rpq_server *s) {
+    cudaSetDevice(s->g->device);
+    int step = 0;
+    bool tables_dirty = true;
+    for (;;) {
+        std::vector<int> admitted;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            auto busy = [&] {
+                for (int i = 0; i < s->lanes_max; i++)
+                    if (s->lane[i].busy) return true;
+                return false;
+            };
+            s->cv.wait(lk, [&] { return s->stop || !s->queue.empty() || busy(); });
+            if (s->stop) return;
+            // admission: free lanes take queued queries
+            for (int i = 0; i < s->lanes_max && !s->queue.empty(); i++) {
+                if (s->lane[i].busy) continue;
+                Pending q = std::move(s->queue.front());
+                s->queue.pop_front();
+                if (q.a.start_mask == 0) {  // empty language from the start: empty answer
+                    finish_ticket(s, q.ticket, RPQ_OK, {}, q.t_submit);
+                    s->cv_done.notify_all();
+                    i--;
+                    continue;
+                }
+                Lane &L = s->lane[i];
+                L.busy = true;
+                L.finished = false;
+                L.ticket = q.ticket;
+                L.a = std::move(q.a);
+                L.source = q.source;
+                L.level = 0;
+                L.t_submit = q.t_submit;
+                admitted.push_back(i);
+                s->admitted++;
+            }
+        }
+        rpq_status err = RPQ_OK;
+        if (!admitted.empty()) tables_dirty = true;
+        if (tables_dirty) {
+            err = upload_tables(s);
+            tables_dirty = false;
+        }
+        // seeds of the admitted lanes into the current frontier
+        if (err == RPQ_OK && !admitted.empty()) {
+            std::map<std::tuple<int, int, int>, uint64_t> seedm;
+            std::vector<int32_t> verts;
+            for (int i : admitted) {
+                const Lane &L = s->lane[i];
+                for (int q = 0; q < L.a.S; q++)
+                    if ((L.a.start_mask >> q) & 1)
+                        seedm[std::make_tuple(L.source, q, i / 64)] |= 1ull << (i % 64);
+                verts.push_back(L.source);
+            }
+            std::sort(verts.begin(), verts.end());
+            verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+            std::vector<int32_t> rec;
+            for (auto &kv : seedm) {
+                rec.push_back(std::get<0>(kv.first));
+                rec.push_back(std::get<1>(kv.first));
+                rec.push_back(std::get<2>(kv.first));
+                rec.push_back((int32_t)(uint32_t)kv.second);
+                rec.push_back((int32_t)(uint32_t)(kv.second >> 32));
+            }
+            uint8_t *hs = static_cast<uint8_t *>(s->staging);
+            memcpy(hs + s->o_seed, rec.data(), sizeof(int32_t) * rec.size());
+            memcpy(hs + s->o_verts, verts.data(), sizeof(int32_t) * verts.size());
+            cudaError_t e = cudaMemcpyAsync(s->tables.as<uint8_t>() + s->o_seed, hs + s->o_seed,
+                                            sizeof(int32_t) * rec.size(), cudaMemcpyHostToDevice,
+                                            s->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s->tables.as<uint8_t>() + s->o_verts, hs + s->o_verts,
+                                    sizeof(int32_t) * verts.size(), cudaMemcpyHostToDevice, s->st);
+            if (e != cudaSuccess) err = fail(RPQ_ERR_CUDA, "seed upload: %s", cudaGetErrorString(e));
+            if (err == RPQ_OK)
+                err = lane_seed(s->p, reinterpret_cast<const int32_t *>(s->tables.as<uint8_t>() + s->o_seed),
+                                (int)(rec.size() / 5),
+                                reinterpret_cast<const int32_t *>(s->tables.as<uint8_t>() + s->o_verts),
+                                (int)verts.size(), step, s->st);
+        }
+        // one level step for every lane
+        if (err == RPQ_OK) {
+            cudaError_t e = cudaGraphLaunch(s->step_exec, s->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s->out_host, s->step_out.p, sizeof(LaneStepOut),
+                                    cudaMemcpyDeviceToHost, s->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+            if (e != cudaSuccess) err = fail(RPQ_ERR_CUDA, "level step: %s", cudaGetErrorString(e));
+            else if (s->out_host->status != 0) err = (rpq_status)s->out_host->status;
+        }
+        std::vector<int32_t> done_ids;
+        if (err == RPQ_OK) {
+            step = s->out_host->step;
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->level_steps++;
+            for (int i = 0; i < s->lanes_max; i++) {
+                Lane &L = s->lane[i];
+                if (!L.busy) continue;
+                L.level++;
+                const bool grew = (s->out_host->lane_new[i / 64] >> (i % 64)) & 1ull;
+                if (!grew || (s->max_levels > 0 && L.level >= s->max_levels)) {
+                    L.finished = true;
+                    done_ids.push_back(i);
+                }
+            }
+        }
+        if (err == RPQ_OK && !done_ids.empty()) {
+            std::vector<int64_t> offs;
+            std::vector<int32_t> ans;
+            err = lane_harvest(s->g, s->ws.get(), s->p,
+                               reinterpret_cast<const uint64_t *>(s->tables.as<uint8_t>() + s->o_fm),
+                               done_ids.data(), (int)done_ids.size(), &offs, &ans, s->st);
+            if (err == RPQ_OK) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (size_t k = 0; k < done_ids.size(); k++) {
+                    Lane &L = s->lane[done_ids[k]];
+                    std::vector<int32_t> a(ans.begin() + offs[k], ans.begin() + offs[k + 1]);
+                    finish_ticket(s, L.ticket, RPQ_OK, std::move(a), L.t_submit);
+                    L.busy = false;
+                    L.finished = false;
+                }
+                tables_dirty = true;
+            }
+            s->cv_done.notify_all();
+        }
+        if (err != RPQ_OK) {
+            // fail every query in flight; the server stops serving
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->fatal = err;
+            for (int i = 0; i < s->lanes_max; i++)
+                if (s->lane[i].busy) {
+                    finish_ticket(s, s->lane[i].ticket, err, {}, s->lane[i].t_submit);
+                    s->lane[i].busy = false;
+                }
+            while (!s->queue.empty()) {
+                finish_ticket(s, s->queue.front().ticket, err, {}, s->queue.front().t_submit);
+                s->queue.pop_front();
+            }
+            s->cv_done.notify_all();
+            return;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace rpq
+
+using namespace rpq;
+
+extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_config *cfg,
+                                       rpq_server **out) {
+    clear_error();
+    if (!g || !out) return fail(RPQ_ERR_INVALID, "null argument");
+    *out = nullptr;
+    rpq_serve_config c{};
+    if (cfg) c = *cfg;
+    const int lanes = c.max_lanes ? c.max_lanes : kLanes;
+    if (lanes <= 0 || lanes > kLanes) return fail(RPQ_ERR_INVALID, "max_lanes must be in [1, %d]", kLanes);
+    const int K = c.max_states ? c.max_states : 16;
+    if (K <= 0 || K > kLaneMaxSlots) return fail(RPQ_ERR_INVALID, "max_states must be in [1, %d]", kLaneMaxSlots);
+    if (c.max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
+    std::unique_ptr<rpq_server> s(new rpq_server());
+    s->g = const_cast<rpq_graph *>(g);
+    s->lanes_max = lanes;
+    s->max_levels = c.max_levels;
+    s->queue_cap = c.queue_capacity > 0 ? (size_t)c.queue_capacity : 65536;
+    RPQ_CUDA_TRY(cudaSetDevice(g->device));
+    // memory: the lane arrays dominate (4 arrays of n x K x 256 bits)
+    int Kc = 4;
+    while (Kc < K) Kc *= 2;
+    const double bytes = 4.0 * g->n * Kc * kLW * 8 + 4.0 * kLanes * ((g->n + 31) / 32) +
+                         3.0 * 4 * g->n + kServeTablesBytes;
+    if (c.memory_budget > 0 && bytes > (double)c.memory_budget)
+        return fail(RPQ_ERR_OOM, "server state needs %.0f bytes, budget %lld", bytes,
+                    (long long)c.memory_budget);
+    rpq_status st = lane_ws_acquire_fixed(s->g, K, &s->ws);
+    if (st != RPQ_OK) return st;
+    s->K = s->ws->K;
+    // table space: dyn | dirs | units | srcs | fmask | seeds | seed vertices
+    s->o_dyn = 0;
+    s->o_dirs = 256;
+    s->o_units = s->o_dirs + (64u << 10);
+    s->o_srcs = s->o_units + (512u << 10);
+    s->o_fm = s->o_srcs + (2u << 20);
+    s->o_seed = s->o_fm + (size_t)kLaneMaxSlots * kLW * 8;
+    s->o_verts = s->o_seed + (size_t)kLanes * kLaneMaxSlots * 5 * 4;
+    if (s->o_verts + kLanes * 4 > kServeTablesBytes) return fail(RPQ_ERR_INVALID, "table layout");
+    if (!s->tables.alloc(kServeTablesBytes) || !s->step_out.alloc(sizeof(LaneStepOut)))
+        return fail(RPQ_ERR_OOM, "server buffers");
+    RPQ_CUDA_TRY(cudaMallocHost(&s->staging, kServeTablesBytes));
+    RPQ_CUDA_TRY(cudaMallocHost((void **)&s->out_host, sizeof(LaneStepOut)));
+    memset(s->staging, 0, kServeTablesBytes);
+    RPQ_CUDA_TRY(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+    // clean lane state
+    const size_t words = (size_t)g->n * s->K * kLW;
+    RPQ_CUDA_TRY(cudaMemsetAsync(s->ws->P.p, 0, words * 8, s->st));
+    RPQ_CUDA_TRY(cudaMemsetAsync(s->ws->M0.p, 0, words * 8, s->st));
+    RPQ_CUDA_TRY(cudaMemsetAsync(s->ws->M1.p, 0, words * 8, s->st));
+    RPQ_CUDA_TRY(cudaMemsetAsync(s->ws->ctr.p, 0, sizeof(LaneCounters), s->st));
+    RPQ_CUDA_TRY(cudaMemsetAsync(s->tables.p, 0, kServeTablesBytes, s->st));
+    s->p = lane_params(s->g, s->ws.get(), 0, 0, 0, 0);
+    uint8_t *dt = s->tables.as<uint8_t>();
+    s->p.dyn = reinterpret_cast<const LaneDyn *>(dt + s->o_dyn);
+    s->p.dirs = reinterpret_cast<const LDir *>(dt + s->o_dirs);
+    s->p.units = reinterpret_cast<const LUnit *>(dt + s->o_units);
+    s->p.srcs = reinterpret_cast<const LSrc *>(dt + s->o_srcs);
+    st = lane_capture_step(s->p, s->step_out.as<LaneStepOut>(), s->st, &s->step_exec);
+    if (st != RPQ_OK) return st;
+    RPQ_CUDA_TRY(cudaStreamSynchronize(s->st));
+    rpq_server *raw = s.get();
+    s->worker = std::thread(worker_main, raw);
+    *out = s.release();
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_serve_submit(rpq_server *s, const rpq_nfa *nfa, int32_t source,
+                                       uint64_t *ticket) {
+    clear_error();
+    if (!s || !nfa || !ticket) return fail(RPQ_ERR_INVALID, "null argument");
+    const Automaton &a = nfa->a;
+    if (source < 0 || source >= s->g->n)
+        return fail(RPQ_ERR_INVALID, "source %d outside [0, %d)", source, s->g->n);
+    if (a.S > s->K) return fail(RPQ_ERR_INVALID, "automaton has %d states; the server holds %d", a.S, s->K);
+    for (size_t t = 0; t < a.sym.size(); t++) {
+        const int lab = a.sym[t] < a.L ? a.sym[t] : a.sym[t] - a.L;
+        if (lab >= s->g->L) return fail(RPQ_ERR_INVALID, "label %d is not a label of the graph", lab);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fatal != RPQ_OK) return fail(s->fatal, "server stopped after a device error");
+    if (s->queue.size() >= s->queue_cap) {
+        s->rejected++;
+        return fail(RPQ_ERR_BUSY, "queue full");
+    }
+    Pending q;
+    q.ticket = s->next_ticket++;
+    q.a = a;
+    q.source = source;
+    q.t_submit = Clock::now();
+    if (!s->started) {
+        s->started = true;
+        s->t_first = q.t_submit;
+    }
+    *ticket = q.ticket;
+    s->inflight[q.ticket] = 1;
+    s->queue.push_back(std::move(q));
+    s->submitted++;
+    s->cv.notify_one();
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_serve_poll(rpq_server *s, uint64_t ticket, int32_t *out_vertices,
+                                     int64_t capacity, int64_t *out_count) {
+    clear_error();
+    if (!s || !out_count || capacity < 0 || (capacity > 0 && !out_vertices))
+        return fail(RPQ_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) {
+        if (s->inflight.count(ticket)) return RPQ_ERR_BUSY;
+        return fail(RPQ_ERR_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    }
+    if (it->second.status != RPQ_OK) {
+        const rpq_status e = it->second.status;
+        s->results.erase(it);
+        return fail(e, "query failed on the device");
+    }
+    const int64_t n = (int64_t)it->second.answer.size();
+    *out_count = n;
+    if (n > capacity) return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices", (long long)n);
+    if (n) {
+        if (is_device_pointer(out_vertices)) {
+            if (cudaMemcpy(out_vertices, it->second.answer.data(), 4 * n, cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+                return fail(RPQ_ERR_CUDA, "copy to device output");
+        } else {
+            memcpy(out_vertices, it->second.answer.data(), 4 * n);
+        }
+    }
+    s->results.erase(it);
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_serve_drain(rpq_server *s, int64_t timeout_ms) {
+    clear_error();
+    if (!s) return fail(RPQ_ERR_INVALID, "null argument");
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                        [&] { return s->inflight.empty(); });
+    if (!ok) return fail(RPQ_ERR_TIMEOUT, "%zu queries still in flight", s->inflight.size());
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_serve_stats_get(rpq_server *s, rpq_serve_stats *out) {
+    clear_error();
+    if (!s || !out) return fail(RPQ_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    rpq_serve_stats r{};
+    r.submitted = s->submitted;
+    r.admitted = s->admitted;
+    r.completed = s->completed;
+    r.rejected = s->rejected;
+    r.level_steps = s->level_steps;
+    if (!s->latency_ms.empty()) {
+        std::vector<double> v = s->latency_ms;
+        std::sort(v.begin(), v.end());
+        r.p50_ms = v[v.size() / 2];
+        r.p99_ms = v[std::min(v.size() - 1, (size_t)(0.99 * (double)v.size()))];
+        double sum = 0;
+        for (double x : v) sum += x;
+        r.mean_ms = sum / (double)v.size();
+    }
+    if (s->started && s->completed > 0) {
+        r.elapsed_s = std::chrono::duration<double>(s->t_last - s->t_first).count();
+        r.qps = r.elapsed_s > 0 ? (double)s->completed / r.elapsed_s : 0.0;
+    }
+    *out = r;
+    return RPQ_OK;
+}
+
+extern "C" void rpq_serve_destroy(rpq_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    if (s->st) cudaStreamSynchronize(s->st);
+    if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+    if (s->staging) cudaFreeHost(s->staging);
+    if (s->out_host) cudaFreeHost(s->out_host);
+    if (s->ws) {
+        // leave the workspace clean for the next user
+        const size_t words = (size_t)s->g->n * s->ws->K * kLW;
+        cudaMemsetAsync(s->ws->P.p, 0, words * 8, s->st);
+        cudaMemsetAsync(s->ws->M0.p, 0, words * 8, s->st);
+        cudaMemsetAsync(s->ws->M1.p, 0, words * 8, s->st);
+        cudaMemsetAsync(s->ws->ctr.p, 0, sizeof(LaneCounters), s->st);
+        cudaStreamSynchronize(s->st);
+        lane_ws_return(s->g, std::move(s->ws));
+    }
+    if (s->st) cudaStreamDestroy(s->st);
+    delete s;
+}

@@ -1,0 +1,130 @@
+"""Serving (continuous batching) against the CPU oracle.
+
+Queries submitted while others are in flight join at the next level step;
+each answer must equal the oracle's, and must be the same whether the query
+ran alone or in the mix."""
+
+import time
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle.regex_nfa import Nfa, compile_regex as oracle_compile
+from paper_2412_10287_gb300 import rpq as R
+from paper_2412_10287_gb300 import workloads as W
+
+from conftest import gpu_available
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def need_gpu():
+    if not gpu_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_10287_gb300 import build as B
+
+    B.build()
+
+
+@pytest.fixture(scope="module")
+def setup():
+    g = W.rmat_graph(13, 60000, 4, seed=71)
+    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+    return g, gg, og
+
+
+TEXTS = ["0*", "1/0*", "(0|1)*/2", "^0/1*", "(0/1)*", "0/1/(2|3)*", "(^0|1)+", "3", "2/^2",
+         "0/1/2/3/(0|1)*", "(0/1/2)*"]
+
+
+def run_server(srv, jobs, stagger_s=0.0):
+    tickets = []
+    for nfa, s in jobs:
+        tickets.append(srv.submit(nfa, s))
+        if stagger_s:
+            time.sleep(stagger_s)
+    srv.drain(120000)
+    return [srv.poll(t) for t in tickets]
+
+
+def test_serve_mixed_and_staggered(setup):
+    g, gg, og = setup
+    srcs = W.below(72, 1, 180, g.n).tolist()
+    jobs = [(R.rpq_nfa_compile(TEXTS[i % len(TEXTS)], 4), srcs[i]) for i in range(180)]
+    exp = [og.ssr(oracle_compile(TEXTS[i % len(TEXTS)], 4), srcs[i])["answer"].tolist()
+           for i in range(180)]
+    srv = R.Server(gg, max_lanes=64, max_states=16)
+    try:
+        got = run_server(srv, jobs)  # 180 queries, 64 lanes: admitted as lanes free up
+        assert [a.tolist() for a in got] == exp
+        got = run_server(srv, jobs[:60], stagger_s=0.0005)  # joining mid-flight
+        assert [a.tolist() for a in got] == exp[:60]
+        st = srv.stats()
+        assert st["completed"] == 240 and st["level_steps"] > 0 and st["p99_ms"] >= st["p50_ms"]
+    finally:
+        srv.close()
+
+
+def test_serve_alone_equals_in_mix(setup):
+    g, gg, og = setup
+    srcs = W.below(73, 1, 40, g.n).tolist()
+    jobs = [(R.rpq_nfa_compile(TEXTS[(3 * i) % len(TEXTS)], 4), srcs[i]) for i in range(40)]
+    srv = R.Server(gg, max_lanes=256, max_states=16)
+    try:
+        mix = run_server(srv, jobs)
+        alone = [run_server(srv, [j])[0] for j in jobs[:12]]
+        for a, b in zip(alone, mix[:12]):
+            assert a.tolist() == b.tolist()
+        single = [R.rpq_query(gg, nfa, s) for nfa, s in jobs[:12]]
+        for a, b in zip(single, mix[:12]):
+            assert a.tolist() == b.tolist()
+    finally:
+        srv.close()
+
+
+def test_serve_transition_automata_and_level_cap(setup):
+    g, gg, og = setup
+    autos = [W.tiny_automaton(800 + i, 4, max_states=6, max_trans=12) for i in range(50)]
+    srcs = W.below(74, 1, 50, g.n).tolist()
+    for cap in (2, 0):
+        srv = R.Server(gg, max_lanes=128, max_states=8, max_levels=cap)
+        try:
+            jobs = [(R.rpq_nfa_from_transitions(S, 4, tr, st, fi), srcs[i])
+                    for i, (S, tr, st, fi) in enumerate(autos)]
+            got = run_server(srv, jobs)
+            for i, (S, tr, st, fi) in enumerate(autos):
+                exp = og.ssr(Nfa(S, 4, tr, st, fi), srcs[i], cap)["answer"]
+                assert got[i].tolist() == exp.tolist(), (i, cap)
+        finally:
+            srv.close()
+
+
+def test_serve_queue_limit_and_errors(setup):
+    g, gg, og = setup
+    srv = R.Server(gg, max_lanes=64, max_states=16, queue_capacity=4)
+    try:
+        nfa = R.rpq_nfa_compile("(0|1|2|3)*", 4)
+        accepted, busy = [], 0
+        srcs = W.below(75, 1, 400, g.n).tolist()
+        for s in srcs:
+            try:
+                accepted.append((srv.submit(nfa, s), s))
+            except R.RpqError as e:
+                assert e.status == R.RPQ_ERR_BUSY
+                busy += 1
+        srv.drain(120000)
+        on = oracle_compile("(0|1|2|3)*", 4)
+        for t, s in accepted[:40]:
+            assert srv.poll(t).tolist() == og.ssr(on, s)["answer"].tolist()
+        assert srv.stats()["rejected"] == busy
+        with pytest.raises(R.RpqError):
+            srv.submit(nfa, g.n)  # source out of range
+        with pytest.raises(R.RpqError):
+            srv.submit(R.rpq_nfa_compile("/".join(["0"] * 20), 4), 0)  # 21 states > 16 slots
+        with pytest.raises(R.RpqError):
+            srv.poll(10 ** 9)  # unknown ticket
+    finally:
+        srv.close()
