@@ -50,10 +50,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "batch", "serve"],
-                    help="rmat20: single queries (the default line); batch: 256 mixed queries "
-                         "per launch; serve: Poisson arrivals through the server")
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "kb20m", "batch", "serve"],
+                    help="rmat20: single queries (the default line); kb20m: single queries on "
+                         "the 20M-vertex knowledge-base graph; batch: 256 mixed queries per "
+                         "launch; serve: Poisson arrivals through the server")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--one-query", default=None,
+                    help="profiling case: run this regex once for warm-up and once more "
+                         "(with --source) on the workload's graph, print its counters, exit")
+    ap.add_argument("--source", type=int, default=0)
     return ap.parse_args()
 
 
@@ -147,17 +152,26 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def workload(per_template):
+def workload(per_template, name="rmat20"):
     from paper_2412_10287_gb300 import workloads as W
 
+    if name == "kb20m":
+        return W.config3(per_template=per_template)
     return W.config2(per_template=per_template)
 
 
 def workload_config(w, n_queries, extra=None):
-    c = {"workload": "rmat20: R-MAT scale 20 (1,048,576 vertices, 2^24 edge samples, "
-                     "a=0.57 b=c=0.19), 8 labels Zipf(1.0), seed 1; "
-                     f"{n_queries} single-source queries (a*, a.b*, (a|b)*.c, a^-.b*), "
-                     "one at a time",
+    if w.name == "kb20m":
+        desc = ("kb20m: Chung-Lu power-law graph, 20,000,000 vertices, 200,000,000 edges "
+                "(out-degree exponent 2.1), 500 labels Zipf(1.1), seed 2; "
+                f"{n_queries} single-source queries (a/b*/c, (a|^b)+, a*/b*, chains, (a/b)*, "
+                "a/(b|^c)*/d), one at a time")
+    else:
+        desc = ("rmat20: R-MAT scale 20 (1,048,576 vertices, 2^24 edge samples, "
+                "a=0.57 b=c=0.19), 8 labels Zipf(1.0), seed 1; "
+                f"{n_queries} single-source queries (a*, a.b*, (a|b)*.c, a^-.b*), "
+                "one at a time")
+    c = {"workload": desc,
          "n_vertices": w.graph.n, "n_edge_samples": w.graph.m, "n_labels": w.graph.n_labels,
          "queries_per_step": n_queries,
          "l2": "flushed between steps (256 MiB write)",
@@ -386,7 +400,24 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload != "rmat20":
+    if args.one_query is not None:
+        import torch
+
+        torch.cuda.set_device(0)
+        import __graft_entry__
+
+        __graft_entry__.build()
+        from paper_2412_10287_gb300 import rpq as R
+        from paper_2412_10287_gb300 import workloads as W
+
+        g = W.config3_graph() if args.workload == "kb20m" else W.config2_graph()
+        gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+        nfa = R.rpq_nfa_compile(args.one_query, g.n_labels)
+        for _ in range(2):
+            _, st = R.rpq_query(gg, nfa, args.source, with_stats=True)
+        print(json.dumps({"query": args.one_query, "source": args.source, "stats": st}))
+        return
+    if args.workload in ("batch", "serve"):
         import torch
 
         torch.cuda.set_device(0)
@@ -414,7 +445,8 @@ def main():
     __graft_entry__.build()
     from paper_2412_10287_gb300 import rpq as R
 
-    w = workload(args.per_template)
+    w = workload(args.per_template if args.workload == "rmat20" else min(args.per_template, 25),
+                 args.workload)
     g = w.graph
     gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
     nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
@@ -424,6 +456,9 @@ def main():
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     W_words = (g.n + 63) // 64
+    if args.workload == "kb20m":
+        global PROFILE_JSON
+        PROFILE_JSON = os.path.join(ROOT, "profiles", "rpq_query_kernel_kb20m.json")
 
     def one_step(collect):
         res = []

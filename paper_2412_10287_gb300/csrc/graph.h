@@ -37,6 +37,10 @@ struct rpq_graph {
     rpq::DevBuf csr_nbr, csc_nbr;  // distinct neighbour ids, label-major
     std::vector<std::unique_ptr<rpq::DevBuf>> owned;  // offsets / hypersparse rows
 
+    // push/pull threshold used by single queries (set by rpq_graph_autotune)
+    float pull_alpha = 4.0f;
+    int32_t pull_min = 256;
+
     std::mutex ws_mu;
     std::vector<std::unique_ptr<rpq::WorkspaceBase>> ws_free;
 

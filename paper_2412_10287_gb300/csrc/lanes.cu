@@ -36,8 +36,8 @@ namespace {
 
 constexpr int kLThreads = 256;
 constexpr int kLWarps = kLThreads / 32;
-constexpr int kLaneHub = 2048;    // edges of one (vertex, direction) handled inline
-constexpr int kLaneChunk = 2048;  // edges per hub chunk
+constexpr int kLaneHub = 128;     // edges of one (vertex, direction) handled inline
+constexpr int kLaneChunk = 128;   // edges per chunk of a longer row (one warp, 4 rounds)
 constexpr uint64_t kLaneBarrierNs = 4000000000ull;
 
 __device__ __forceinline__ int32_t *lane_list(const LParams &p, int idx) {
@@ -108,6 +108,8 @@ __device__ bool lane_aggregate(const LParams &p, const LDir &dir, const uint64_t
 }
 
 // Pushes the frontier lanes sm_X along edges [b, e) of direction dir.  Whole warp.
+// Per edge and target slot, the 4 visited words (one 32-byte sector) are
+// loaded as two 16-byte vectors; only lane words with new bits are OR-ed.
 __device__ void lane_push(const LParams &p, const LDir &dir, const uint64_t *sm_X, int32_t b,
                           int32_t e, int32_t *TV, unsigned long long *tvc) {
     const int32_t *nbr = p.adj[dir.d].nbr;
@@ -118,18 +120,19 @@ __device__ void lane_push(const LParams &p, const LDir &dir, const uint64_t *sm_
         const int32_t w = valid ? __ldg(nbr + k) : 0;
         bool first = false;
         for (int uu = 0; uu < dir.unit_count; uu++) {
+            const uint64_t x0 = sm_X[uu * kLW + 0], x1 = sm_X[uu * kLW + 1];
+            const uint64_t x2 = sm_X[uu * kLW + 2], x3 = sm_X[uu * kLW + 3];
+            if (!(x0 | x1 | x2 | x3) || !valid) continue;
             const int k2 = p.units[dir.unit_first + uu].k2;
             const size_t row = ((size_t)w * p.K + k2) * kLW;
+            const ulonglong2 pa = __ldcg(reinterpret_cast<const ulonglong2 *>(p.P + row));
+            const ulonglong2 pb = __ldcg(reinterpret_cast<const ulonglong2 *>(p.P + row) + 1);
+            const uint64_t y[kLW] = {x0 & ~pa.x, x1 & ~pa.y, x2 & ~pb.x, x3 & ~pb.y};
 #pragma unroll
             for (int lw = 0; lw < kLW; lw++) {
-                const uint64_t x = sm_X[uu * kLW + lw];
-                if (!x || !valid) continue;
-                uint64_t y = x & ~__ldcg(p.P + row + lw);
-                if (!y) continue;
-                y &= ~__ldcg(p.NX + row + lw);
-                if (!y) continue;
+                if (!y[lw]) continue;
                 const unsigned long long old =
-                    atomicOr((unsigned long long *)(p.NX + row + lw), (unsigned long long)y);
+                    atomicOr((unsigned long long *)(p.NX + row + lw), (unsigned long long)y[lw]);
                 if (old == 0ull) first = true;
             }
         }
@@ -158,11 +161,9 @@ __device__ void lane_expand_vertices(const LParams &p, int j, uint64_t *sm_M, ui
     int32_t *TV = lane_list(p, nxt);
     unsigned long long *tvc = &p.c->list_count[nxt];
     const unsigned lane = lane_id();
-    for (;;) {
-        unsigned long long i = 0;
-        if (lane == 0) i = atomicAdd(&p.c->claim_v, 1ull);
-        i = __shfl_sync(kFull, i, 0);
-        if (i >= nA) break;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long i = (unsigned long long)gw; i < nA; i += (unsigned long long)nw) {
         const int32_t v = __ldcg(A + i);
         lane_load_row(p, M, v, sm_M);
         const int n_dirs = p.dyn->n_dirs;
@@ -173,14 +174,17 @@ __device__ void lane_expand_vertices(const LParams &p, int j, uint64_t *sm_M, ui
             adj_row(p.adj[dir.d], v, b, e);
             const int32_t e1 = min(e, b + kLaneHub);
             if (e > e1 && lane == 0) {
-                const unsigned long long nch = (unsigned long long)((e - e1 + kLaneChunk - 1) / kLaneChunk);
+                const unsigned long long nch =
+                    (unsigned long long)((e - e1 + kLaneChunk - 1) / kLaneChunk);
                 const unsigned long long old = atomicAdd(&p.c->hub_packed, (1ull << 40) | nch);
                 const long long hi = (long long)(old >> 40);
-                if (hi < p.hub_cap) {
+                const long long cb = (long long)(old & ((1ull << 40) - 1));
+                if (hi < p.hub_cap && cb + (long long)nch <= p.chunk_cap) {
                     LHub h;
                     h.v = v; h.dir = D; h.b = e1; h.e = e;
-                    h.chunk_base = (long long)(old & ((1ull << 40) - 1));
+                    h.chunk_base = cb;
                     p.hubs[hi] = h;
+                    for (unsigned long long k = 0; k < nch; k++) p.hub_cmap[cb + k] = (int32_t)hi;
                 } else {
                     atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
                 }
@@ -201,20 +205,15 @@ __device__ void lane_expand_hubs(const LParams &p, int j, uint64_t *sm_M, uint64
     const long long nh = (long long)(packed >> 40);
     const long long nch = (long long)(packed & ((1ull << 40) - 1));
     const unsigned lane = lane_id();
-    for (;;) {
-        unsigned long long cc = 0;
-        if (lane == 0) cc = atomicAdd(&p.c->claim_h, 1ull);
-        const long long c = (long long)__shfl_sync(kFull, cc, 0);
-        if (c >= nch) break;
-        long long lo = 0, hi = nh - 1;
-        while (lo < hi) {
-            const long long mid = (lo + hi + 1) >> 1;
-            if (__ldcg(&p.hubs[mid].chunk_base) <= c) lo = mid; else hi = mid - 1;
-        }
-        const int32_t v = __ldcg(&p.hubs[lo].v);
-        const int D = __ldcg(&p.hubs[lo].dir);
-        const int32_t hb = __ldcg(&p.hubs[lo].b), he = __ldcg(&p.hubs[lo].e);
-        const long long base = __ldcg(&p.hubs[lo].chunk_base);
+    (void)nh;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = gw; c < nch; c += nw) {
+        const int hi = __ldcg(p.hub_cmap + c);
+        const int32_t v = __ldcg(&p.hubs[hi].v);
+        const int D = __ldcg(&p.hubs[hi].dir);
+        const int32_t hb = __ldcg(&p.hubs[hi].b), he = __ldcg(&p.hubs[hi].e);
+        const long long base = __ldcg(&p.hubs[hi].chunk_base);
         const int32_t b = hb + (int32_t)((c - base) * kLaneChunk);
         const int32_t e = min(he, b + kLaneChunk);
         lane_load_row(p, M, v, sm_M);
@@ -222,6 +221,7 @@ __device__ void lane_expand_hubs(const LParams &p, int j, uint64_t *sm_M, uint64
         if (lane_aggregate(p, dir, sm_M, sm_X)) lane_push(p, dir, sm_X, b, e, TV, tvc);
         __syncwarp();
     }
+    (void)lane;
 }
 
 // Commit of level j -> j+1 (grid-stride, a warp per list entry).
@@ -590,16 +590,21 @@ rpq_status lane_ws_alloc(LaneWorkspace *ws, const rpq_graph *g, int K) {
     const size_t tvw = ((size_t)g->n + 63) / 64;
     const int64_t words32 = ((int64_t)g->n + 31) / 32;
     const size_t list_cap = (size_t)g->n + 2 * kLanes;  // distinct vertices + seeds of one step
-    long long hub_cap = 1024;
-    for (int d = 0; d < 2 * g->L; d++) hub_cap += g->adj[d].nnz / kLaneHub + 1;
+    long long hub_cap = 1024, chunk_cap = 1024;
+    for (int d = 0; d < 2 * g->L; d++) {
+        hub_cap += g->adj[d].nnz / kLaneHub + 1;
+        chunk_cap += g->adj[d].nnz / kLaneChunk + 1;
+    }
     ws->n = g->n;
     ws->K = K;
     ws->hub_cap = hub_cap;
+    ws->chunk_cap = chunk_cap;
     const int64_t chunks = (words32 + kCountChunk - 1) / kCountChunk;
     if (!ws->M0.alloc(words * 8) || !ws->M1.alloc(words * 8) || !ws->P.alloc(words * 8) ||
         !ws->NX.alloc(words * 8) || !ws->tv.alloc(tvw * 8) || !ws->l0.alloc(4 * list_cap) ||
         !ws->l1.alloc(4 * list_cap) || !ws->l2.alloc(4 * list_cap) ||
-        !ws->hubs.alloc(sizeof(LHub) * hub_cap) || !ws->ctr.alloc(sizeof(LaneCounters)) ||
+        !ws->hubs.alloc(sizeof(LHub) * hub_cap) ||
+        !ws->hub_cmap.alloc(sizeof(int32_t) * chunk_cap) || !ws->ctr.alloc(sizeof(LaneCounters)) ||
         !ws->tables.alloc(1 << 20) || !ws->A32.alloc((size_t)kLanes * words32 * 4) ||
         !ws->cnt.alloc(sizeof(int64_t) * (kLanes * chunks + 1)) ||
         !ws->pos.alloc(sizeof(int64_t) * (kLanes * chunks + 1)))
@@ -671,7 +676,9 @@ LParams lane_params(rpq_graph *g, LaneWorkspace *ws, size_t o_dyn, size_t o_dirs
     p.list1 = ws->l1.as<int32_t>();
     p.list2 = ws->l2.as<int32_t>();
     p.hubs = ws->hubs.as<LHub>();
+    p.hub_cmap = ws->hub_cmap.as<int32_t>();
     p.hub_cap = ws->hub_cap;
+    p.chunk_cap = ws->chunk_cap;
     p.c = ws->ctr.as<LaneCounters>();
     return p;
 }

@@ -70,15 +70,16 @@ struct LParams {
     uint64_t *tv;                // touched-vertex bitset, ceil(n/64) words
     int32_t *list0, *list1, *list2;
     LHub *hubs;
-    long long hub_cap;
+    int32_t *hub_cmap;           // chunk -> hub entry
+    long long hub_cap, chunk_cap;
     LaneCounters *c;
 };
 
 // Device workspace of one lane group (sized for n vertices and K slots).
 struct LaneWorkspace : WorkspaceBase {
     int32_t n = 0, K = 0;
-    long long hub_cap = 0;
-    DevBuf M0, M1, P, NX, tv, l0, l1, l2, hubs, ctr, tables, A32, cnt, pos;
+    long long hub_cap = 0, chunk_cap = 0;
+    DevBuf M0, M1, P, NX, tv, l0, l1, l2, hubs, hub_cmap, ctr, tables, A32, cnt, pos;
     void *staging = nullptr;
     size_t staging_bytes = 0;
     ~LaneWorkspace() override;

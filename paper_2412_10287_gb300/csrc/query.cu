@@ -1352,8 +1352,8 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
     p.max_levels = max_levels;
     p.start_mask = a.start_mask;
     p.final_mask = a.final_mask;
-    p.alpha = env_float("RPQ_PULL_ALPHA", 4.0f);
-    p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", 256.0f);
+    p.alpha = env_float("RPQ_PULL_ALPHA", g->pull_alpha);
+    p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
     p.groups = reinterpret_cast<const QGroup *>(dt + o_groups);
     p.units = reinterpret_cast<const QUnit *>(dt + o_units);
     p.t_unit = reinterpret_cast<const int32_t *>(dt + o_tu);
@@ -1448,6 +1448,63 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
 }
 
 }  // namespace rpq
+
+// ------------------------------------------------------------- autotune --
+namespace rpq {
+rpq_status autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas, const int32_t *sources,
+                    float *alpha_out, int32_t *min_out, void *stream) {
+    static const float kAlphas[] = {0.0f, 1.0f, 2.0f, 4.0f, 8.0f, 16.0f, 64.0f};
+    static const int32_t kMins[] = {64, 256, 2048};
+    const float keep_a = g->pull_alpha;
+    const int32_t keep_m = g->pull_min;
+    double best = -1;
+    float best_a = keep_a;
+    int32_t best_m = keep_m;
+    for (float a : kAlphas) {
+        for (int32_t m : kMins) {
+            if (a == 0.0f && m != kMins[0]) continue;  // push only: min_pull is moot
+            g->pull_alpha = a;
+            g->pull_min = m;
+            double total = 0;
+            for (int rep = 0; rep < 2; rep++) {  // first pass warms the workspace
+                total = 0;
+                for (int32_t i = 0; i < n; i++) {
+                    rpq_stats st{};
+                    int64_t cnt = 0;
+                    rpq_status s = run_query(g, nfas[i]->a, sources[i], 0, nullptr, 0, nullptr,
+                                             nullptr, &st, &cnt, stream);
+                    if (s != RPQ_OK) {
+                        g->pull_alpha = keep_a;
+                        g->pull_min = keep_m;
+                        return s;
+                    }
+                    total += st.device_ms;
+                }
+            }
+            if (best < 0 || total < best) {
+                best = total;
+                best_a = a;
+                best_m = m;
+            }
+        }
+    }
+    g->pull_alpha = best_a;
+    g->pull_min = best_m;
+    if (alpha_out) *alpha_out = best_a;
+    if (min_out) *min_out = best_m;
+    return RPQ_OK;
+}
+}  // namespace rpq
+
+extern "C" rpq_status rpq_graph_autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
+                                         const int32_t *sources, float *alpha_out,
+                                         int32_t *min_pull_out, void *stream) {
+    rpq::clear_error();
+    if (!g || n <= 0 || !nfas || !sources) return rpq::fail(RPQ_ERR_INVALID, "bad argument");
+    for (int32_t i = 0; i < n; i++)
+        if (!nfas[i]) return rpq::fail(RPQ_ERR_INVALID, "automaton %d is null", i);
+    return rpq::autotune(g, n, nfas, sources, alpha_out, min_pull_out, stream);
+}
 
 // --------------------------------------------------- no-allocation entry --
 // Scratch for rpq_query_noalloc: a fixed device array that exists for as
@@ -1566,8 +1623,8 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     p.max_levels = max_levels;
     p.start_mask = a.start_mask;
     p.final_mask = a.final_mask;
-    p.alpha = env_float("RPQ_PULL_ALPHA", 4.0f);
-    p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", 256.0f);
+    p.alpha = env_float("RPQ_PULL_ALPHA", g->pull_alpha);
+    p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
     p.groups = reinterpret_cast<const QGroup *>(base + x_tab + o_groups);
     p.units = reinterpret_cast<const QUnit *>(base + x_tab + o_units);
     p.t_unit = reinterpret_cast<const int32_t *>(base + x_tab + o_tu);

@@ -59,6 +59,7 @@ struct Lane {
     Automaton a;
     int32_t source = 0;
     int level = 0;
+    int64_t finished_step = 0;
     Clock::time_point t_submit;
 };
 
@@ -250,21 +251,46 @@ void worker_main(rpq_server *s) {
             if (e != cudaSuccess) err = fail(RPQ_ERR_CUDA, "level step: %s", cudaGetErrorString(e));
             else if (s->out_host->status != 0) err = (rpq_status)s->out_host->status;
         }
-        std::vector<int32_t> done_ids;
+        // lanes whose frontier emptied (or that reached the level cap) stop
+        // expanding at once; their answers are extracted in batches, so the
+        // extract-and-clear pass over the visited set is shared
         if (err == RPQ_OK) {
             step = s->out_host->step;
             std::lock_guard<std::mutex> lk(s->mu);
             s->level_steps++;
             for (int i = 0; i < s->lanes_max; i++) {
                 Lane &L = s->lane[i];
-                if (!L.busy) continue;
+                if (!L.busy || L.finished) continue;
                 L.level++;
                 const bool grew = (s->out_host->lane_new[i / 64] >> (i % 64)) & 1ull;
                 if (!grew || (s->max_levels > 0 && L.level >= s->max_levels)) {
                     L.finished = true;
-                    done_ids.push_back(i);
+                    L.finished_step = s->level_steps;
+                    tables_dirty = true;  // drop the lane from the active mask
                 }
             }
+        }
+        std::vector<int32_t> done_ids;
+        if (err == RPQ_OK) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            int running = 0, free_lanes = 0;
+            int64_t oldest = -1;
+            for (int i = 0; i < s->lanes_max; i++) {
+                const Lane &L = s->lane[i];
+                if (!L.busy) {
+                    free_lanes++;
+                } else if (L.finished) {
+                    done_ids.push_back(i);
+                    if (oldest < 0 || L.finished_step < oldest) oldest = L.finished_step;
+                } else {
+                    running++;
+                }
+            }
+            const bool harvest = !done_ids.empty() &&
+                                 ((int)done_ids.size() >= 16 || running == 0 ||
+                                  (!s->queue.empty() && free_lanes == 0) ||
+                                  s->level_steps - oldest >= 4);
+            if (!harvest) done_ids.clear();
         }
         if (err == RPQ_OK && !done_ids.empty()) {
             std::vector<int64_t> offs;

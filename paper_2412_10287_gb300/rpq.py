@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "RPQ_OK", 1: "RPQ_ERR_INVALID", 2: "RPQ_ERR_PARSE", 3: "RPQ_E
 # Every symbol include/rpq.h declares.
 EXPORTED = (
     "rpq_set_allocator", "rpq_graph_load", "rpq_graph_free", "rpq_graph_info", "rpq_graph_export",
+    "rpq_graph_autotune",
     "rpq_nfa_compile", "rpq_nfa_from_transitions", "rpq_nfa_free", "rpq_nfa_info",
     "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_query_noalloc",
     "rpq_query_bitset",
@@ -93,6 +94,7 @@ def lib():
             "rpq_graph_load": [i32, i32, i64, p, p, p, p, pp],
             "rpq_graph_info": [p, i32, p, p, p],
             "rpq_graph_export": [p, i32, i32, p, p, i64],
+            "rpq_graph_autotune": [p, i32, p, p, p, p, p],
             "rpq_nfa_compile": [ctypes.c_char_p, i32, pp],
             "rpq_nfa_from_transitions": [i32, i32, i32, p, p, p, i32, p, i32, p, pp],
             "rpq_nfa_info": [p, p, p, p],
@@ -247,6 +249,18 @@ def rpq_graph_export(g: Graph, label: int, inverse: bool):
     nbr = np.zeros(max(int(off[-1]), 1), np.int32)
     _check(lib().rpq_graph_export(g.h, label, int(inverse), _ptr(off), _ptr(nbr), nbr.size))
     return off, nbr[: int(off[-1])]
+
+
+def rpq_graph_autotune(g: Graph, nfas, sources, stream=None):
+    """Measures the push/pull threshold on sample queries and stores it in the
+    graph; returns (alpha, min_pull)."""
+    n = len(nfas)
+    handles = (ctypes.c_void_p * n)(*[x.h.value for x in nfas])
+    src, psrc = _host_i32(sources)
+    a, m = ctypes.c_float(), ctypes.c_int32()
+    _check(lib().rpq_graph_autotune(g.h, n, handles, psrc, ctypes.byref(a), ctypes.byref(m),
+                                    _stream_handle(stream)))
+    return a.value, m.value
 
 
 # ------------------------------------------------------------- automaton --

@@ -286,3 +286,19 @@ def test_config2_sampled_parity():
         exp = og.ssr(oracle_compile(q.regex, g.n_labels), q.source)["answer"]
         got = gpu_regex(gg, q.regex, g.n_labels, q.source)
         assert got.tolist() == exp.tolist(), q
+
+
+def test_autotune_keeps_answers():
+    """The autotuner only changes the push/pull threshold; answers and the
+    algorithm's counters must not change."""
+    g = W.rmat_graph(14, 1 << 18, 4, seed=91)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    texts = ["0*", "1/0*", "(0|1)*/2", "^0/1*"]
+    srcs = W.below(92, 1, 8, g.n).tolist()
+    nfas = [R.rpq_nfa_compile(texts[i % 4], 4) for i in range(8)]
+    alpha, mn = R.rpq_graph_autotune(gg, nfas, srcs)
+    assert alpha in (0.0, 1.0, 2.0, 4.0, 8.0, 16.0, 64.0) and mn in (64, 256, 2048)
+    for i in range(8):
+        exp = og.ssr(oracle_compile(texts[i % 4], 4), srcs[i])["answer"]
+        assert R.rpq_query(gg, nfas[i], srcs[i]).tolist() == exp.tolist()
