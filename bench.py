@@ -294,15 +294,63 @@ def run_batch(args, R, torch):
             acc.append(e0.elapsed_time(e1) / 1000.0)
     qb = len(nfas) * args.steps / sum(tb)
     qs = len(nfas) * args.steps / sum(ts)
+    # the same batch forced onto bit lanes, and a shared-automaton batch (one
+    # automaton from 256 sources: the multi-source BFS case lanes are made for)
+    extra = {}
+    for label, env, jobs in (("mixed_on_lanes", "lanes", None),
+                             ("shared_automaton_lanes", None, "shared"),
+                             ("shared_automaton_sequential", None, "shared_seq")):
+        old_env = os.environ.get("RPQ_BATCH_ENGINE")
+        if env:
+            os.environ["RPQ_BATCH_ENGINE"] = env
+        try:
+            if jobs is None:
+                fn = batch_once
+            else:
+                shared = [R.rpq_nfa_compile("0*", g.n_labels)] * len(srcs)
+                sh_handles = (ctypes.c_void_p * len(shared))(*[x.h.value for x in shared])
+                sh_res = R.rpq_query_batch(gg, shared, srcs)
+                sh_out = torch.empty(max(1, sum(a.size for a in sh_res)), dtype=torch.int32,
+                                     device="cuda")
+                if jobs == "shared":
+                    def fn():
+                        st_ = R.lib().rpq_query_batch(gg.h, len(shared), sh_handles,
+                                                      R._ptr(src_arr), 0, R._ptr(offs),
+                                                      R._ptr(sh_out), sh_out.numel(), None,
+                                                      ctypes.c_void_p(stream.cuda_stream))
+                        assert st_ == 0, R.rpq_last_error()
+                else:
+                    def fn():
+                        one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                        for s_ in srcs:
+                            R.rpq_query(gg, shared[0], s_, out=one, stream=stream)
+            fn()
+            ts_ = []
+            for _ in range(args.steps):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                ts_.append(time.perf_counter() - t0)
+            extra[label] = len(srcs) * args.steps / sum(ts_)
+        finally:
+            if env:
+                if old_env is None:
+                    os.environ.pop("RPQ_BATCH_ENGINE", None)
+                else:
+                    os.environ["RPQ_BATCH_ENGINE"] = old_env
     line = {"metric": "rpq_queries_per_s", "value": qb, "unit": "queries/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * sum(tb) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "rmat20_batch: the rmat20 graph; 256 mixed queries per launch "
-                                   f"(DFA states {min(states)}-{max(states)}) packed as uint64 "
-                                   "bit lanes; seed 3",
+            "config": {"workload": "rmat20_batch: the rmat20 graph; 256 mixed queries per "
+                                   f"rpq_query_batch call (DFA states {min(states)}-{max(states)}); "
+                                   "seed 3",
                        "l2": "flushed between steps (256 MiB write)"},
             "sequential_single_queries_per_s": qs, "batch_speedup": qb / qs,
+            "engine": os.environ.get("RPQ_BATCH_ENGINE", "auto (slots for mixed automata)"),
+            "other_engines_queries_per_s": extra,
             "answer_vertices_per_step": int(total), "gpu_launches": None}
     print(json.dumps(line), flush=True)
 
@@ -322,12 +370,14 @@ def run_serve(args, R, torch):
         if q.regex not in nfas:
             nfas[q.regex] = R.rpq_nfa_compile(q.regex, g.n_labels)
     qs = w.queries
-    srv = R.Server(gg, max_lanes=256, max_states=16)
-    # warm-up burst
-    for q in qs[:256]:
-        srv.submit(nfas[q.regex], q.source)
-    srv.drain(600000)
-    srv.close()
+    engines = {"slots": dict(max_lanes=8, engine=0), "lanes": dict(max_lanes=256, max_states=16,
+                                                                    engine=1)}
+    for cfg in engines.values():  # warm-up burst
+        srv = R.Server(gg, **cfg)
+        for q in qs[:256]:
+            srv.submit(nfas[q.regex], q.source)
+        srv.drain(600000)
+        srv.close()
 
     def served(server):
         t0 = time.perf_counter()
@@ -343,9 +393,12 @@ def run_serve(args, R, torch):
             server.poll(t)
         return st
 
-    srv = R.Server(gg, max_lanes=256, max_states=16)
-    st_srv = served(srv)
-    srv.close()
+    served_stats = {}
+    for name, cfg in engines.items():
+        srv = R.Server(gg, **cfg)
+        served_stats[name] = served(srv)
+        srv.close()
+    st_srv = served_stats["slots"]
 
     # unbatched served loop: one query at a time in arrival order
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
@@ -365,14 +418,16 @@ def run_serve(args, R, torch):
 
     # saturation: everything submitted at once
     sat_n = min(len(qs), 4096)
-    srv = R.Server(gg, max_lanes=256, max_states=16)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(nfas[q.regex], q.source) for q in qs[:sat_n]]
-    srv.drain(600000)
-    sat_srv = sat_n / (time.perf_counter() - t0)
-    for t in tickets:
-        srv.poll(t)
-    srv.close()
+    sat = {}
+    for name, cfg in engines.items():
+        srv = R.Server(gg, **cfg)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(nfas[q.regex], q.source) for q in qs[:sat_n]]
+        srv.drain(600000)
+        sat[name] = sat_n / (time.perf_counter() - t0)
+        for t in tickets:
+            srv.poll(t)
+        srv.close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for q in qs[:sat_n]:
@@ -384,12 +439,15 @@ def run_serve(args, R, torch):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"rmat20_serve: Poisson arrivals at 2,000 q/s for "
                                    f"{args.serve_seconds + 1.0:.0f} s ({len(qs)} queries, mixed "
-                                   "templates of 1-12 DFA states), 256 lanes x 16 state slots"},
+                                   "templates of 1-12 DFA states); server engine 0 = 8 "
+                                   "concurrent query slots (value), engine 1 = 256 bit lanes"},
             "p50_ms": st_srv["p50_ms"], "p99_ms": st_srv["p99_ms"],
-            "level_steps": st_srv["level_steps"],
+            "engines": {k: {"qps": v["qps"], "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"]}
+                        for k, v in served_stats.items()},
             "unbatched_served_loop": unb,
-            "saturation_queries_per_s": {"server": sat_srv, "one_at_a_time": sat_seq,
-                                         "queries": sat_n}}
+            "saturation_queries_per_s": {"server_slots": sat["slots"],
+                                         "server_lanes": sat["lanes"],
+                                         "one_at_a_time": sat_seq, "queries": sat_n}}
     print(json.dumps(line), flush=True)
 
 

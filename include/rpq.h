@@ -227,12 +227,16 @@ rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_nfa *const *
 /* ------------------------------------------------------------- serving -- */
 
 typedef struct rpq_serve_config {
-    int32_t max_lanes;       /* queries in flight on the device (multiple of 64; 0 = 256) */
-    int32_t max_states;      /* state slots per lane (0 = 16) */
+    int32_t max_lanes;       /* queries in flight on the device: query slots for engine 0
+                                (0 = 8, at most 64), bit lanes for engine 1 (0 = 256) */
+    int32_t max_states;      /* state slots per lane, engine 1 (0 = 16) */
     int32_t queue_capacity;  /* submitted-but-not-admitted queries (0 = 65536) */
     int64_t memory_budget;   /* bytes of device state the server may hold (0 = no limit) */
     int32_t max_levels;      /* per-query level cap (0 = none) */
-    int32_t reserved;
+    int32_t engine;          /* 0: concurrent query slots -- each admitted query runs the
+                                single-query kernel on its own stream and 1/slots of the SMs;
+                                1: bit lanes -- every admitted query advances one level per
+                                replay of a captured CUDA graph of the lane step */
 } rpq_serve_config;
 
 typedef struct rpq_serve_stats {
@@ -244,13 +248,17 @@ typedef struct rpq_serve_stats {
     double qps;              /* completed / elapsed_s */
 } rpq_serve_stats;
 
-/* A server keeps the graph and every admitted query's state on the device
- * and runs a host thread that (1) admits queued queries into free lanes while
- * device memory allows, (2) advances every active lane by one level per step
- * (a captured CUDA graph replay), (3) retires lanes whose frontier emptied and
- * stores their answers.  Queries arriving while others run join at the next
- * level step (continuous batching); each answer is the same as the query
- * alone would give. */
+/* A server keeps the graph and every admitted query's state on the device;
+ * queries arriving while others run are admitted as soon as a slot or lane
+ * frees up, and their work overlaps on the device (continuous batching).
+ * Engine 0: `max_lanes` host workers each run one admitted query at a time
+ * with the persistent query kernel on their own stream and a share of the
+ * SMs.  Engine 1: a host thread (1) admits queued queries into free bit
+ * lanes, (2) advances every active lane by one level per step (a captured
+ * CUDA graph replay), (3) retires lanes whose frontier emptied and stores
+ * their answers.  Each answer is the same as the query alone would give.
+ * Device memory is bounded by the slot/lane count (memory_budget is checked
+ * at creation). */
 rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_config *cfg, rpq_server **out);
 
 /* Non-blocking.  RPQ_ERR_BUSY when the queue is full.  The automaton must

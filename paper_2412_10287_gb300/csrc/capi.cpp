@@ -37,6 +37,8 @@ rpq_status fail(rpq_status st, const char *fmt, ...) {
 
 void clear_error() { t_error.clear(); }
 
+const char *rpq_last_error_str() { return t_error.c_str(); }
+
 void *dev_alloc(size_t bytes) {
     if (g_alloc.alloc) return g_alloc.alloc(bytes, g_alloc.ctx);
     void *p = nullptr;

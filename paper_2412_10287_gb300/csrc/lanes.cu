@@ -17,6 +17,9 @@
 // The answer of lane i is {v : P[v][k] has bit i for a final slot k of i}.
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <string>
+#include <thread>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -955,6 +958,114 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     return RPQ_OK;
 }
 
+rpq_status bitsets_to_lists(const uint32_t *bits, int64_t words32, int count, int32_t *out,
+                            bool out_is_dev, int64_t capacity, int64_t *offsets, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    offsets[0] = 0;
+    if (count == 0) return RPQ_OK;
+    const int64_t chunks = (words32 + kCountChunk - 1) / kCountChunk;
+    const long long nblk = (long long)count * chunks;
+    DevBuf cnt, pos;
+    if (!cnt.alloc(sizeof(int64_t) * (nblk + 1)) || !pos.alloc(sizeof(int64_t) * (nblk + 1)))
+        return fail(RPQ_ERR_OOM, "answer compaction buffers");
+    lane_count_kernel<<<(unsigned)nblk, 256, 0, st>>>(bits, words32, count, chunks,
+                                                     cnt.as<int64_t>());
+    RPQ_CUDA_TRY(cudaGetLastError());
+    rpq_status s = device_exclusive_scan<int64_t>(cnt.as<int64_t>(), pos.as<int64_t>(), nblk,
+                                                  pos.as<int64_t>() + nblk, st);
+    if (s != RPQ_OK) return s;
+    std::vector<int64_t> hpos((size_t)nblk + 1);
+    RPQ_CUDA_TRY(cudaMemcpyAsync(hpos.data(), pos.p, sizeof(int64_t) * (nblk + 1),
+                                 cudaMemcpyDeviceToHost, st));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < count; i++) offsets[i] = hpos[(size_t)i * chunks];
+    offsets[count] = hpos[nblk];
+    const int64_t total = hpos[nblk];
+    if (total == 0 || total > capacity) return RPQ_OK;
+    if (out_is_dev) {
+        lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(bits, words32, count, chunks,
+                                                           pos.as<int64_t>(), out, capacity);
+        RPQ_CUDA_TRY(cudaGetLastError());
+        RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+        return RPQ_OK;
+    }
+    DevBuf tmp;
+    if (!tmp.alloc(sizeof(int32_t) * total)) return fail(RPQ_ERR_OOM, "answer staging");
+    lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(bits, words32, count, chunks,
+                                                       pos.as<int64_t>(), tmp.as<int32_t>(), total);
+    RPQ_CUDA_TRY(cudaGetLastError());
+    RPQ_CUDA_TRY(cudaMemcpyAsync(out, tmp.p, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, st));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    return RPQ_OK;
+}
+
+// Batch by query slots: `slots` concurrent persistent query kernels, each on
+// 1/slots of the grid and its own stream, take the queries in turn; every
+// answer lands as a bitset row, and the rows become sorted lists at the end.
+rpq_status slot_batch(rpq_graph *g, const Automaton *const *autos, const int32_t *sources,
+                      int n, int32_t max_levels, int slots, int32_t *out, bool out_is_dev,
+                      int64_t capacity, int64_t *offsets, rpq_stats *stats, cudaStream_t st) {
+    const int64_t W = ((int64_t)g->n + 63) / 64;
+    DevBuf bits;
+    if (!bits.alloc(sizeof(uint64_t) * (size_t)W * std::max(n, 1)))
+        return fail(RPQ_ERR_OOM, "answer bitsets of %d queries", n);
+    // callers' earlier work on `st` must be visible to the slot streams
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    std::atomic<int> next{0};
+    std::atomic<int> first_err{(int)RPQ_OK};
+    std::mutex msg_mu;
+    std::string msg;
+    auto worker = [&]() {
+        cudaSetDevice(g->device);
+        cudaStream_t s2 = nullptr;
+        if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+            first_err = (int)RPQ_ERR_CUDA;
+            return;
+        }
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= n || first_err.load() != (int)RPQ_OK) break;
+            int64_t cnt = 0;
+            rpq_stats local{};
+            const rpq_status r = run_query_slot(g, *autos[i], sources[i], max_levels, nullptr, 0,
+                                                bits.as<uint64_t>() + (size_t)i * W, nullptr,
+                                                stats ? &local : nullptr, &cnt, s2, slots);
+            if (r != RPQ_OK) {
+                int expect = (int)RPQ_OK;
+                if (first_err.compare_exchange_strong(expect, (int)r)) {
+                    std::lock_guard<std::mutex> lk(msg_mu);
+                    msg = rpq_last_error_str();
+                }
+                break;
+            }
+            if (stats) stats[i] = local;
+        }
+        cudaStreamSynchronize(s2);
+        cudaStreamDestroy(s2);
+    };
+    std::vector<std::thread> th;
+    for (int k = 0; k < slots; k++) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    if (first_err.load() != (int)RPQ_OK)
+        return fail((rpq_status)first_err.load(), "%s", msg.c_str());
+    return bitsets_to_lists(reinterpret_cast<const uint32_t *>(bits.p), 2 * W, n, out, out_is_dev,
+                            capacity, offsets, st);
+}
+
+bool same_automaton(const Automaton &a, const Automaton &b) {
+    if (a.S != b.S || a.L != b.L || a.start_mask != b.start_mask || a.final_mask != b.final_mask ||
+        a.from.size() != b.from.size())
+        return false;
+    std::vector<std::tuple<int, int, int>> x, y;
+    for (size_t t = 0; t < a.from.size(); t++) {
+        x.emplace_back(a.from[t], a.sym[t], a.to[t]);
+        y.emplace_back(b.from[t], b.sym[t], b.to[t]);
+    }
+    std::sort(x.begin(), x.end());
+    std::sort(y.begin(), y.end());
+    return x == y;
+}
+
 }  // namespace rpq
 
 using namespace rpq;
@@ -978,7 +1089,27 @@ extern "C" rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_n
     bool overflow = false;
     std::vector<const Automaton *> autos(n);
     for (int i = 0; i < n; i++) autos[i] = &nfas[i]->a;
-    for (int g0 = 0; g0 < n; g0 += kLanes) {
+    // engine: bit lanes pay off when the queries share their automaton (their
+    // frontiers then overlap level by level: multi-source BFS); otherwise
+    // concurrent query slots use the GPU better
+    bool shared = n >= 16;
+    for (int i = 1; i < n && shared; i++) shared = same_automaton(*autos[0], *autos[i]);
+    const char *eng = getenv("RPQ_BATCH_ENGINE");
+    const bool use_lanes = eng ? strcmp(eng, "lanes") == 0 : shared;
+    if (!use_lanes) {
+        const char *sl = getenv("RPQ_SLOTS");
+        const int slots = std::max(1, std::min(64, sl ? atoi(sl) : 8));
+        for (int i = 0; i < n; i++)
+            if (sources[i] < 0 || sources[i] >= gm->n)
+                return fail(RPQ_ERR_INVALID, "query %d: source %d outside [0, %d)", i, sources[i],
+                            gm->n);
+        rpq_status s = slot_batch(gm, autos.data(), sources, n, max_levels, std::min(slots, std::max(n, 1)),
+                                  out_vertices, dev, capacity, out_offsets, stats, st);
+        if (s != RPQ_OK) return s;
+        total = out_offsets[n];
+        overflow = total > capacity;
+    }
+    for (int g0 = 0; use_lanes && g0 < n; g0 += kLanes) {
         const int cnt = std::min(kLanes, n - g0);
         std::vector<int64_t> offs(cnt + 1);
         std::vector<int32_t> lv(cnt);

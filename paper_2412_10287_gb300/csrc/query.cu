@@ -1305,6 +1305,16 @@ float env_float(const char *name, float dflt) {
 rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
                      int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
                      int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream) {
+    return run_query_slot(g, a, source, max_levels, out_list_dev, capacity, out_bits_dev,
+                          out_host_list, stats, count, stream, 1);
+}
+
+// As run_query, on 1/grid_div of the persistent grid, so that grid_div
+// queries can run concurrently on separate streams.
+rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
+                          int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
+                          int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
+                          int grid_div) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (source < 0 || source >= g->n)
         return fail(RPQ_ERR_INVALID, "source %d outside [0, %d)", source, g->n);
@@ -1401,6 +1411,7 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
         return s;
     }
     if (grid > 152 * 64) grid = 152 * 64;
+    if (grid_div > 1) grid = std::max(1, grid / grid_div);
     RPQ_CUDA_TRY(cudaMemsetAsync(&p.c->status, 0, sizeof(int32_t), st));
     const bool timed = stats != nullptr;
     if (timed) RPQ_CUDA_TRY(cudaEventRecord(ws->ev0, st));

@@ -17,6 +17,7 @@ namespace rpq {
 // Records a message for rpq_last_error() on this thread and returns `st`.
 rpq_status fail(rpq_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 void clear_error();
+const char *rpq_last_error_str();  // this thread's last message
 
 // ------------------------------------------------------------- allocator --
 void *dev_alloc(size_t bytes);  // nullptr on failure
@@ -72,6 +73,16 @@ rpq_status device_exclusive_scan(const T *in, int64_t *out, int64_t n, int64_t *
 rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
                      int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
                      int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream);
+rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
+                          int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
+                          int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
+                          int grid_div);
+
+// Sorted vertex lists of `count` answer bitsets (row i at bits + i * words32
+// uint32 words) into out (host or device, capacity entries); offsets
+// (count + 1) on the host.  lanes.cu.
+rpq_status bitsets_to_lists(const uint32_t *bits, int64_t words32, int count, int32_t *out,
+                            bool out_is_dev, int64_t capacity, int64_t *offsets, void *stream);
 
 }  // namespace rpq
 

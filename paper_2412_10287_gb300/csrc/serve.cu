@@ -68,7 +68,9 @@ struct Lane {
 
 struct rpq_server {
     rpq_graph *g = nullptr;
+    int engine = 0;
     int lanes_max = 0, K = 0, max_levels = 0;
+    std::vector<std::thread> slot_workers;
     size_t queue_cap = 0;
     std::unique_ptr<rpq::LaneWorkspace> ws;
     cudaStream_t st = nullptr;
@@ -330,6 +332,44 @@ void worker_main(rpq_server *s) {
     }
 }
 
+// Engine 0: one admitted query at a time per worker, on its own stream and
+// 1/lanes_max of the persistent grid.
+void slot_worker_main(rpq_server *s) {
+    cudaSetDevice(s->g->device);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->fatal = RPQ_ERR_CUDA;
+        return;
+    }
+    std::vector<int32_t> buf((size_t)s->g->n);
+    for (;;) {
+        Pending q;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            if (s->stop) break;
+            q = std::move(s->queue.front());
+            s->queue.pop_front();
+            s->admitted++;
+        }
+        int64_t cnt = 0;
+        const rpq_status r = run_query_slot(s->g, q.a, q.source, s->max_levels, nullptr,
+                                            (int64_t)buf.size(), nullptr, buf.data(), nullptr,
+                                            &cnt, st, s->lanes_max);
+        std::vector<int32_t> ans;
+        if (r == RPQ_OK) ans.assign(buf.begin(), buf.begin() + cnt);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            finish_ticket(s, q.ticket, r, std::move(ans), q.t_submit);
+            s->level_steps++;
+        }
+        s->cv_done.notify_all();
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+}
+
 }  // namespace
 }  // namespace rpq
 
@@ -342,6 +382,28 @@ extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_confi
     *out = nullptr;
     rpq_serve_config c{};
     if (cfg) c = *cfg;
+    if (c.engine != 0 && c.engine != 1) return fail(RPQ_ERR_INVALID, "engine must be 0 or 1");
+    if (c.engine == 0) {
+        const int slots = c.max_lanes ? c.max_lanes : 8;
+        if (slots <= 0 || slots > 64) return fail(RPQ_ERR_INVALID, "max_lanes (slots) must be in [1, 64]");
+        if (c.max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
+        std::unique_ptr<rpq_server> s(new rpq_server());
+        s->g = const_cast<rpq_graph *>(g);
+        s->engine = 0;
+        s->lanes_max = slots;
+        s->K = kMaxStates;
+        s->max_levels = c.max_levels;
+        s->queue_cap = c.queue_capacity > 0 ? (size_t)c.queue_capacity : 65536;
+        // a slot holds one query workspace: 4 bitsets + 3 vertex lists per state
+        const double per_slot = 16.0 * ((g->n + 63) / 64) * 8 * 4 + 16.0 * g->n * 4 * 3;
+        if (c.memory_budget > 0 && per_slot * slots > (double)c.memory_budget)
+            return fail(RPQ_ERR_OOM, "%d slots need about %.0f bytes, budget %lld", slots,
+                        per_slot * slots, (long long)c.memory_budget);
+        rpq_server *raw = s.get();
+        for (int k = 0; k < slots; k++) s->slot_workers.emplace_back(slot_worker_main, raw);
+        *out = s.release();
+        return RPQ_OK;
+    }
     const int lanes = c.max_lanes ? c.max_lanes : kLanes;
     if (lanes <= 0 || lanes > kLanes) return fail(RPQ_ERR_INVALID, "max_lanes must be in [1, %d]", kLanes);
     const int K = c.max_states ? c.max_states : 16;
@@ -513,6 +575,8 @@ extern "C" void rpq_serve_destroy(rpq_server *s) {
     }
     s->cv.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    for (auto &t : s->slot_workers)
+        if (t.joinable()) t.join();
     if (s->st) cudaStreamSynchronize(s->st);
     if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
     if (s->staging) cudaFreeHost(s->staging);

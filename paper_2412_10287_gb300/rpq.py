@@ -60,7 +60,7 @@ class RpqStats(ctypes.Structure):
 class RpqServeConfig(ctypes.Structure):
     _fields_ = [("max_lanes", ctypes.c_int32), ("max_states", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
-                ("max_levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_levels", ctypes.c_int32), ("engine", ctypes.c_int32)]
 
 
 class RpqServeStats(ctypes.Structure):
@@ -416,8 +416,9 @@ def rpq_query_batch(g: Graph, nfas, sources, max_levels: int = 0, stream=None,
 
 class Server:
     def __init__(self, g: Graph, max_lanes=0, max_states=0, queue_capacity=0, memory_budget=0,
-                 max_levels=0):
-        cfg = RpqServeConfig(max_lanes, max_states, queue_capacity, memory_budget, max_levels, 0)
+                 max_levels=0, engine=0):
+        cfg = RpqServeConfig(max_lanes, max_states, queue_capacity, memory_budget, max_levels,
+                             engine)
         out = ctypes.c_void_p()
         _check(lib().rpq_serve_create(g.h, ctypes.byref(cfg), ctypes.byref(out)))
         self.h = out

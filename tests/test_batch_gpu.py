@@ -28,6 +28,33 @@ def load(g):
     return R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
 
 
+@pytest.fixture(params=["slots", "lanes"], autouse=True)
+def engine(request):
+    """Every batch test runs on both engines: concurrent query slots and bit lanes."""
+    import os
+
+    old = os.environ.get("RPQ_BATCH_ENGINE")
+    os.environ["RPQ_BATCH_ENGINE"] = request.param
+    yield request.param
+    if old is None:
+        os.environ.pop("RPQ_BATCH_ENGINE", None)
+    else:
+        os.environ["RPQ_BATCH_ENGINE"] = old
+
+
+def test_batch_shared_automaton_many_sources():
+    """One automaton from many sources (multi-source BFS): every answer equals the oracle's."""
+    g = W.rmat_graph(14, 1 << 18, 4, seed=35)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    srcs = W.below(36, 1, 200, g.n).tolist()
+    nfa = R.rpq_nfa_compile("(0|^1)*/2", 4)
+    got = R.rpq_query_batch(gg, [nfa] * 200, srcs)
+    on = oracle_compile("(0|^1)*/2", 4)
+    for i in range(0, 200, 7):
+        assert got[i].tolist() == og.ssr(on, srcs[i])["answer"].tolist(), i
+
+
 def test_batch_tiny_mixed():
     for seed in range(12):
         g = W.tiny_graph(seed + 3000, max_n=16, max_m=40)
