@@ -59,6 +59,10 @@ def parse():
                     help="profiling case: run this regex once for warm-up and once more "
                          "(with --source) on the workload's graph, print its counters, exit")
     ap.add_argument("--source", type=int, default=0)
+    ap.add_argument("--write-profile", default=None, metavar="NCU_CSV",
+                    help="read an ncu CSV of traversal-kernel launches taken with --metrics "
+                         "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum and "
+                         "write the per-launch DRAM traffic file of --workload, then exit")
     return ap.parse_args()
 
 
@@ -93,6 +97,56 @@ def profile_traffic():
         return pj.get("dram_bytes_per_launch")
     except Exception:
         return None
+
+
+UNIT_SCALE = {"": 1.0, "k": 1e3, "K": 1e3, "M": 1e6, "G": 1e9, "T": 1e12,
+              "n": 1e-9, "u": 1e-6, "m": 1e-3}
+
+
+def ncu_value(unit, value):
+    """A metric value of an ncu CSV in base units (bytes, seconds)."""
+    v = float(str(value).replace(",", ""))
+    u = unit.strip()
+    for base in ("byte", "second", "s"):
+        if u.endswith(base):
+            return v * UNIT_SCALE.get(u[: -len(base)], 1.0)
+    return v
+
+
+def write_profile(csv_path, workload_name):
+    """Per-launch DRAM bytes and ncu durations of the traversal kernel, from an
+    ncu CSV, written beside the kernel source's hash so that a later change
+    to the kernel voids the figure."""
+    import csv
+
+    launches = {}
+    with open(csv_path, newline="") as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        if "rpq_query_kernel" not in row.get("Kernel Name", ""):
+            continue
+        d = launches.setdefault(row["ID"], {})
+        d[row["Metric Name"]] = ncu_value(row.get("Metric Unit", ""), row["Metric Value"])
+    per = [d for d in launches.values()
+           if "dram__bytes_read.sum" in d and "dram__bytes_write.sum" in d]
+    if not per:
+        raise SystemExit(f"no rpq_query_kernel launches with DRAM metrics in {csv_path}")
+    rd = sum(d["dram__bytes_read.sum"] for d in per) / len(per)
+    wr = sum(d["dram__bytes_write.sum"] for d in per) / len(per)
+    dur = [d["gpu__time_duration.sum"] for d in per if "gpu__time_duration.sum" in d]
+    out = {
+        "kernel": "rpq_query_kernel", "workload": workload_name, "launches": len(per),
+        "kernel_source_sha256": sha256(KERNEL_SOURCE),
+        "dram_bytes_per_launch": rd + wr, "dram_read_bytes_per_launch": rd,
+        "dram_write_bytes_per_launch": wr,
+        "ncu_ms_per_launch": (sum(dur) / len(dur) * 1e3) if dur else None,
+        "note": "ncu flushes caches before each profiled launch: cold-cache figures",
+    }
+    path = os.path.join(ROOT, "profiles", f"rpq_query_kernel_{workload_name}.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out))
 
 
 class ClockSampler:
@@ -457,6 +511,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.write_profile:
+        write_profile(args.write_profile, args.workload)
         return
     if args.one_query is not None:
         import torch
