@@ -40,6 +40,10 @@ struct rpq_graph {
     // push/pull threshold used by single queries (set by rpq_graph_autotune)
     float pull_alpha = 4.0f;
     int32_t pull_min = 256;
+    // a level runs on one CTA, with no grid barrier, while its push edge mass
+    // and frontier items stay within these (solo_mass < 0: never)
+    int32_t solo_mass = 2048;
+    int32_t solo_items = 256;
 
     std::mutex ws_mu;
     std::vector<std::unique_ptr<rpq::WorkspaceBase>> ws_free;

@@ -3,8 +3,12 @@
 //     answer F x P
 // run as ONE persistent cooperative kernel per query.  The Boolean matrices
 // are bitsets with one row of |V| bits per automaton state (P: visited,
-// F_j: the frontier M_j), and the frontier is also kept as per-state vertex
-// lists.  Each level j is one grid-wide phase followed by one grid barrier:
+// F_j: the frontier M_j).  Every visited pair is also appended, in discovery
+// order, to an append-only list per state, so that level j's frontier of
+// state q is one contiguous range of q's list.  A level runs either on the
+// whole grid (one grid-wide phase, then one grid barrier) or, while the
+// frontier is small, on CTA 0 alone with no grid barrier at all, the other
+// CTAs parked at a gate until CTA 0 needs them again:
 //
 //   expand j   for every (label direction d, target state q'):
 //     push     for every frontier pair (q, v) with q -d-> q' and every w in
@@ -23,8 +27,14 @@
 //   decide j+1 (every CTA, same data): stop when M_{j+1} is empty or the level
 //   cap is reached; else pick push or pull per (d, q').
 //
-// Every wait on other CTAs (the grid barrier) is bounded by a wall-clock
-// limit; on expiry the kernel records RPQ_ERR_TIMEOUT and returns.
+// The answer F x P is either swept from P by the grid or, when it is small,
+// gathered from the final states' lists and sorted by CTA 0.  The kernel
+// leaves P and the F bitsets all-zero when it ends (cleared through the
+// lists, or densely where that is cheaper), so the next query on the same
+// workspace starts without an O(S |V|) clear.
+//
+// Every wait on other CTAs (the grid barrier, the gate) is bounded by a
+// wall-clock limit; on expiry the kernel records RPQ_ERR_TIMEOUT and returns.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -42,7 +52,7 @@ constexpr int kR = 4;                 // edges per lane per round in the batched
 constexpr int kWarpRow = rpq_graph::kLongRow;  // rows with at least this many edges are chunked
 constexpr int kChunk = 32 * kR;       // edges per chunk: one warp round
 static_assert(kChunk == rpq_graph::kLongChunk, "chunk size must match the graph's row statistics");
-constexpr int kClaimChunks = 4;       // chunks a warp claims at once
+constexpr int kPullBatch = 8;         // in-neighbours a pull lane tests per round trip
 constexpr int kGather = 1024;         // gather buffer entries per CTA
 constexpr int kMaxGroups = 512;
 constexpr int kMaxUnits = 512;
@@ -75,13 +85,33 @@ struct Row {
 // slot j % 3 holds level j.
 struct Counters {
     unsigned bar_count, bar_gen;
-    int32_t status, pad0;
+    int32_t status, gate_cmd;
+    int32_t pub_level, pad0;
+    unsigned long long gate;  // (launch epoch << 32) | releases of the gate so far
+    unsigned long long beat;  // CTA 0's progress while it runs levels alone
+    unsigned long long parked;  // CTAs that have parked (cumulative over the launch)
+    // level state CTA 0 publishes when it releases the gate into a level
+    long long pub_vstart[kMaxStates], pub_vprev[kMaxStates], pub_flprev[kMaxStates];
     unsigned long long fl_count[3][kMaxStates];  // frontier pairs per state
     unsigned long long rows_packed[3];           // (rows << 40) | chunks
     unsigned long long lvl_bytes[3], lvl_edges[3];
     unsigned long long claim_chunk[3], claim_item[3], claim_pull[3];
     long long levels, visited, expanded, product_edges, push_bytes;
     long long push_units, pull_units, answer_count;
+};
+
+// Automaton tables of up to this many bytes travel inside the kernel's
+// parameters (no host-to-device copy before the launch).
+constexpr int kInlineTables = 2048;
+
+// Query summary CTA 0 writes to host-mapped memory when the kernel ends, so
+// the host reads it (after synchronising the stream) without a device-to-host
+// copy.  A failed launch writes none: `epoch` then differs from the launch's.
+struct QueryResult {
+    long long levels, visited, expanded, product_edges, push_bytes;
+    long long push_units, pull_units, answer_count;
+    uint32_t epoch;
+    int32_t pad;
 };
 
 struct KParams {
@@ -92,6 +122,10 @@ struct KParams {
     uint64_t start_mask, final_mask;
     float alpha;       // pull when frontier edge mass * alpha > in-adjacency edges + rows
     int32_t min_pull;  // ... and the unit's source frontier holds at least this many pairs
+    int32_t solo_mass;   // a level runs on CTA 0 alone when its push edge mass <= this,
+    int32_t solo_items;  // its frontier items <= this and no unit pulls (solo_mass < 0: never)
+    uint32_t epoch;      // distinct per launch on this workspace (tags the gate word)
+    int32_t clear_first; // P and F hold garbage: clear them before the traversal
     // automaton tables (device)
     const QGroup *groups;
     const QUnit *units;
@@ -101,7 +135,7 @@ struct KParams {
     // state (device)
     uint64_t *P;             // [S][W]
     uint64_t *F[3];          // [S][W] per level slot
-    int32_t *FL[3];          // [S][n] per level slot
+    int32_t *VL;             // [S][n] visited vertices of each state, in discovery order
     Row *rows[3];            // long rows per level slot
     int32_t *cmap[3];        // chunk -> row index per level slot
     long long row_cap, chunk_cap;
@@ -115,9 +149,13 @@ struct KParams {
     // optional per-level trace (block 0's view)
     unsigned long long *trace;
     int32_t trace_cap;
+    QueryResult *result;  // host-mapped summary, or null
+    // tables inside the parameters: byte offsets into tab (when tab_inline)
+    int32_t tab_inline, o_groups, o_units, o_tu, o_ts, o_ug;
+    alignas(16) uint8_t tab[kInlineTables];
 };
 
-constexpr int kTraceFields = 8;  // t_decide, t_expand, t_barrier, pairs, push units, pull units
+constexpr int kTraceFields = 8;  // t_plan, t_expand, t_barrier, pairs, push units, pull units, grid
 constexpr int kTraceLevels = 4096;
 
 __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsigned long long v) {
@@ -130,7 +168,7 @@ __device__ __forceinline__ int load_status(const Counters *c) {
     return *(volatile const int32_t *)&c->status;
 }
 
-__device__ bool grid_barrier(Counters *c) {
+__device__ __forceinline__ bool grid_barrier(Counters *c) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *genp = &c->bar_gen;
@@ -177,10 +215,15 @@ struct Shared {
     int32_t *t_unit, *t_state, *u_group;
     unsigned long long *fl;       // [kMaxStates] pairs per state at the current level
     unsigned long long *fl_prev;  // [kMaxStates] at the previous level
+    long long *vstart;            // [kMaxStates] current level's first list entry
+    long long *vprev;             // [kMaxStates] previous level's first list entry
+    long long *vnext;             // [kMaxStates] next level's first list entry
     unsigned long long *mfv;      // [n_groups]
     unsigned long long *s_mf;     // [n_groups] per-CTA edge mass of discoveries
     int32_t *gbuf_k;
     int16_t *gbuf_g;
+    unsigned long long *lvl;      // [2] level's push bytes / product edges (CTA 0's statistics)
+    int32_t *flags;               // [2] test P before the atomicOr (big levels); spare
 };
 
 template <class F>
@@ -210,7 +253,12 @@ __host__ __device__ size_t shared_layout(int ng, int nu, int nt, int nug, F take
     take(22, sizeof(unsigned long long) * ng);
     take(23, sizeof(unsigned long long) * ng);
     take(24, sizeof(int32_t) * kGather);
-    return take(25, sizeof(int16_t) * kGather);
+    take(25, sizeof(int16_t) * kGather);
+    take(26, sizeof(long long) * kMaxStates);
+    take(27, sizeof(long long) * kMaxStates);
+    take(28, sizeof(long long) * kMaxStates);
+    take(29, sizeof(unsigned long long) * 2);
+    return take(30, sizeof(int32_t) * 2);
 }
 
 __host__ __device__ size_t shared_bytes(int ng, int nu, int nt, int nug) {
@@ -224,7 +272,7 @@ __host__ __device__ size_t shared_bytes(int ng, int nu, int nt, int nug) {
 
 __device__ Shared carve(const KParams &p, uint8_t *base) {
     Shared s;
-    uint8_t *ptr[26];
+    uint8_t *ptr[31];
     size_t off = 0;
     shared_layout(p.n_groups, p.n_units, p.n_targets, p.n_ugroups, [&](int i, size_t bytes) {
         off = (off + 15) & ~size_t(15);
@@ -258,12 +306,28 @@ __device__ Shared carve(const KParams &p, uint8_t *base) {
     s.s_mf = (unsigned long long *)ptr[23];
     s.gbuf_k = (int32_t *)ptr[24];
     s.gbuf_g = (int16_t *)ptr[25];
+    s.vstart = (long long *)ptr[26];
+    s.vprev = (long long *)ptr[27];
+    s.vnext = (long long *)ptr[28];
+    s.lvl = (unsigned long long *)ptr[29];
+    s.flags = (int32_t *)ptr[30];
     return s;
 }
 
 __device__ void load_tables(const KParams &p, const Shared &sh) {
+    const QGroup *groups = p.groups;
+    const QUnit *units = p.units;
+    const int32_t *t_unit = p.t_unit, *t_state = p.t_state, *u_group = p.u_group;
+    if (p.tab_inline) {  // the parameter block is grid-constant: its address is usable
+        const uint8_t *b = p.tab;
+        groups = reinterpret_cast<const QGroup *>(b + p.o_groups);
+        units = reinterpret_cast<const QUnit *>(b + p.o_units);
+        t_unit = reinterpret_cast<const int32_t *>(b + p.o_tu);
+        t_state = reinterpret_cast<const int32_t *>(b + p.o_ts);
+        u_group = reinterpret_cast<const int32_t *>(b + p.o_ug);
+    }
     for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
-        const QGroup G = p.groups[g];
+        const QGroup G = groups[g];
         sh.gq[g] = G.q;
         sh.gd[g] = G.d;
         sh.gnbr[g] = p.adj[G.d].nbr;
@@ -274,7 +338,7 @@ __device__ void load_tables(const KParams &p, const Shared &sh) {
         sh.s_mf[g] = 0;
     }
     for (int u = threadIdx.x; u < p.n_units; u += kThreads) {
-        const QUnit U = p.units[u];
+        const QUnit U = units[u];
         sh.urows[u] = U.in_rows;
         sh.unnz[u] = U.in_nnz;
         sh.ug_first[u] = U.g_first;
@@ -285,13 +349,20 @@ __device__ void load_tables(const KParams &p, const Shared &sh) {
         sh.upull[u] = 0;
     }
     for (int i = threadIdx.x; i < p.n_targets; i += kThreads) {
-        sh.t_unit[i] = p.t_unit[i];
-        sh.t_state[i] = p.t_state[i];
+        sh.t_unit[i] = t_unit[i];
+        sh.t_state[i] = t_state[i];
     }
-    for (int i = threadIdx.x; i < p.n_ugroups; i += kThreads) sh.u_group[i] = p.u_group[i];
+    for (int i = threadIdx.x; i < p.n_ugroups; i += kThreads) sh.u_group[i] = u_group[i];
     for (int q = threadIdx.x; q < kMaxStates; q += kThreads) {
         sh.fl[q] = 0;
         sh.fl_prev[q] = 0;
+        sh.vstart[q] = 0;
+        sh.vprev[q] = 0;
+        sh.vnext[q] = 0;
+    }
+    if (threadIdx.x < 2) {
+        sh.lvl[threadIdx.x] = 0;
+        sh.flags[threadIdx.x] = 0;
     }
     __syncthreads();
 }
@@ -299,15 +370,16 @@ __device__ void load_tables(const KParams &p, const Shared &sh) {
 // ------------------------------------------------------------ discovery --
 struct LevelCtx {
     int slot;                     // slot of the level being discovered
-    int32_t *FL;
-    uint64_t *F;
+    int32_t *VL;
+    const long long *vnext;       // first list entry of the level being discovered
+    uint64_t *F;                  // frontier bits of that level, or null (not kept)
     Row *rows;
     int32_t *cmap;
     unsigned long long *s_acc;    // [2] per-CTA push bytes / product edges
 };
 
 // Lanes with `found` have discovered the new pair (q2, w) of the next level.
-// Appends it to the frontier list of q2, sets its frontier bit, and measures
+// Appends it to the visited list of q2, sets its frontier bit, and measures
 // its rows for every group leaving q2 (gsf[q2] .. gsf[q2+1]).  q2 must be
 // warp-uniform; all 32 lanes must call.
 __device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t *gsf,
@@ -321,9 +393,10 @@ __device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t 
         base = atomicAdd(&p.c->fl_count[L.slot][q2], (unsigned long long)__popc(m));
     base = __shfl_sync(kFull, base, leader);
     if (found) {
-        L.FL[(size_t)q2 * p.n + base + __popc(m & lanemask_lt())] = w;
-        atomicOr((unsigned long long *)(L.F + (size_t)q2 * p.W + ((uint32_t)w >> 6)),
-                 1ull << (w & 63));
+        L.VL[(size_t)q2 * p.n + L.vnext[q2] + base + __popc(m & lanemask_lt())] = w;
+        if (L.F)
+            atomicOr((unsigned long long *)(L.F + (size_t)q2 * p.W + ((uint32_t)w >> 6)),
+                     1ull << (w & 63));
     }
     unsigned long long acc_b = 0, acc_e = 0;
     for (int g = gsf[q2]; g < gsf[q2 + 1]; g++) {
@@ -389,14 +462,15 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&p.c->fl_count[L.slot][q2], (unsigned long long)total);
     base = __shfl_sync(kFull, base, 0);
-    int32_t *lst = L.FL + (size_t)q2 * p.n;
-    uint64_t *Fq = L.F + (size_t)q2 * p.W;
+    int32_t *lst = L.VL + (size_t)q2 * p.n + L.vnext[q2];
+    uint64_t *Fq = L.F ? L.F + (size_t)q2 * p.W : nullptr;
     unsigned long long run = base;
 #pragma unroll
     for (int r = 0; r < kB; r++) {
         if (found[r]) {
             lst[run + __popc(m[r] & lanemask_lt())] = w[r];
-            atomicOr((unsigned long long *)(Fq + ((uint32_t)w[r] >> 6)), 1ull << (w[r] & 63));
+            if (Fq)
+                atomicOr((unsigned long long *)(Fq + ((uint32_t)w[r] >> 6)), 1ull << (w[r] & 63));
         }
         run += __popc(m[r]);
     }
@@ -509,10 +583,11 @@ __device__ __forceinline__ void relax_batch(const KParams &p, const Shared &sh, 
     uint64_t *Pq = p.P + (size_t)q2 * p.W;
     bool act[kR];
     uint64_t pw[kR];
+    const bool pre = sh.flags[0] != 0;  // on big levels most targets are visited: test first
 #pragma unroll
     for (int r = 0; r < kR; r++) {
         act[r] = valid[r] && ((tm[r] >> q2) & 1ull);
-        pw[r] = act[r] ? __ldcg(Pq + ((uint32_t)w[r] >> 6)) : ~0ull;
+        pw[r] = (act[r] && pre) ? __ldcg(Pq + ((uint32_t)w[r] >> 6)) : (act[r] ? 0ull : ~0ull);
     }
 #pragma unroll
     for (int r = 0; r < kR; r++) {
@@ -528,42 +603,48 @@ __device__ __forceinline__ void relax_batch(const KParams &p, const Shared &sh, 
 }
 
 // ---------------------------------------------------------------- phases -
-// Tile claims: the first tile of every CTA is static, later ones come from a
-// counter that therefore starts past the static ones.  CTA-uniform result.
+// Tile claims of CTA `cta` of `ncta` working CTAs: the first tile of every
+// CTA is static, later ones come from a counter that therefore starts past
+// the static ones; a CTA working alone just steps.  CTA-uniform result.
 __device__ __forceinline__ long long claim_block(unsigned long long *ctr, long long *s_claim,
-                                                 bool first, long long tile) {
-    if (first) return (long long)blockIdx.x * tile;
+                                                 int k, long long tile, int cta, int ncta) {
+    if (k == 0) return (long long)cta * tile;
+    if (ncta == 1) return (long long)k * tile;
     if (threadIdx.x == 0)
-        *s_claim = (long long)gridDim.x * tile + (long long)atomicAdd(ctr, (unsigned long long)tile);
+        *s_claim = (long long)ncta * tile + (long long)atomicAdd(ctr, (unsigned long long)tile);
     __syncthreads();
     const long long t = *s_claim;
     __syncthreads();
     return t;
 }
 
+// Level j on CTA `cta` of `ncta` working CTAs (the whole grid, or CTA 0
+// alone for a small level).  Frontier bits (read only by pull) are kept for
+// the levels a grid level (`on_grid`) discovers; `clear_prev`: level j-1's
+// bits exist and are cleared here.
 __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const int32_t *gsf,
-                             long long *s_claim, unsigned long long *s_acc) {
+                             long long *s_claim, unsigned long long *s_acc, int cta, int ncta,
+                             bool on_grid, bool clear_prev) {
     const int cs = j % 3, ns = (j + 1) % 3, os = (j + 2) % 3;
     const uint64_t *F = p.F[cs];
-    const int32_t *FL = p.FL[cs];
-    LevelCtx L{ns, p.FL[ns], p.F[ns], p.rows[ns], p.cmap[ns], s_acc};
+    LevelCtx L{ns, p.VL, sh.vnext, on_grid ? p.F[ns] : nullptr, p.rows[ns], p.cmap[ns], s_acc};
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
 
-    // housekeeping: clear F of level j-1 (slot os) through its vertex lists
+    // housekeeping: clear F of level j-1 (slot os) through its list range
     // and reset slot os's counters (nothing else touches slot os now)
-    if (j >= 1) {
+    if (clear_prev) {
         for (int q = 0; q < p.S; q++) {
             const unsigned long long cnt = sh.fl_prev[q];
-            const int32_t *lst = p.FL[os] + (size_t)q * p.n;
+            const int32_t *lst = p.VL + (size_t)q * p.n + sh.vprev[q];
             uint64_t *Fo = p.F[os] + (size_t)q * p.W;
-            for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
-                 i < cnt; i += (unsigned long long)gridDim.x * kThreads)
+            for (unsigned long long i = (unsigned long long)cta * kThreads + threadIdx.x; i < cnt;
+                 i += (unsigned long long)ncta * kThreads)
                 Fo[(uint32_t)__ldcg(lst + i) >> 6] = 0;
         }
     }
-    if (blockIdx.x == 0) {
+    if (cta == 0) {
         for (int i = threadIdx.x; i < p.S; i += kThreads) p.c->fl_count[os][i] = 0;
         for (int i = threadIdx.x; i < p.n_groups; i += kThreads) p.mf[os * kMaxGroups + i] = 0;
         if (threadIdx.x == 0) {
@@ -585,9 +666,8 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         const long long nchunks = (long long)(packed & ((1ull << 40) - 1));
         const Row *R = p.rows[cs];
         const int32_t *CM = p.cmap[cs];
-        const long long stride = (long long)gridDim.x * kWarps;
-        for (long long c = (long long)blockIdx.x + (long long)warp * gridDim.x; c < nchunks;
-             c += stride) {
+        const long long stride = (long long)ncta * kWarps;
+        for (long long c = (long long)cta + (long long)warp * ncta; c < nchunks; c += stride) {
             const int ri = __ldcg(CM + c);
             const int g = __ldcg(&R[ri].g);
             const uint64_t tmv = sh.tpush[g];
@@ -611,22 +691,27 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         }
     }
 
-    // (2) short rows of push groups: CTA tiles of frontier items, scan-based gather
+    // (2) short rows of push groups: CTA tiles of frontier items, scan-based
+    //     gather; a small frontier is spread over every CTA (tiles of 8 to
+    //     kThreads items)
     const long long total_items = sh.gpref[p.n_groups];
-    for (bool first = true; total_items > 0; first = false) {
-        const long long t0 = claim_block(&p.c->claim_item[cs], s_claim, first, kThreads);
+    const long long item_tile =
+        min((long long)kThreads, max(8LL, ((total_items + ncta - 1) / ncta + 7) & ~7LL));
+    for (int k = 0; total_items > 0; k++) {
+        const long long t0 = claim_block(&p.c->claim_item[cs], s_claim, k, item_tile, cta, ncta);
         if (t0 >= total_items) break;
         const long long i = t0 + threadIdx.x;
         int g = -1;
         int32_t rb = 0, re = 0;
-        if (i < total_items) {
+        if (threadIdx.x < item_tile && i < total_items) {
             int lo = 0, hi = p.n_groups - 1;  // last group with gpref <= i
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (sh.gpref[mid] <= i) lo = mid; else hi = mid - 1;
             }
             g = lo;
-            const int32_t v = __ldcg(FL + (size_t)sh.gq[g] * p.n + (i - sh.gpref[g]));
+            const int q = sh.gq[g];
+            const int32_t v = __ldcg(p.VL + (size_t)q * p.n + sh.vstart[q] + (i - sh.gpref[g]));
             adj_row(p.adj[sh.gd[g]], v, rb, re);
             if (re - rb >= kWarpRow) re = rb;  // expanded through the chunk list
         }
@@ -686,8 +771,8 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
 
     // (3) pull units: sweep the rows of the in-adjacency
     const long long total_rows = sh.upref[p.n_units];
-    for (bool first = true; total_rows > 0; first = false) {
-        const long long t0 = claim_block(&p.c->claim_pull[cs], s_claim, first, kThreads);
+    for (int k = 0; total_rows > 0; k++) {
+        const long long t0 = claim_block(&p.c->claim_pull[cs], s_claim, k, kThreads, cta, ncta);
         if (t0 >= total_rows) break;
         const long long i = t0 + threadIdx.x;
         int u = 0;
@@ -720,17 +805,26 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         }
         bool found = false, pending = false;
         if (cand) {
+            // up to kWarpRow in-neighbours, kPullBatch at a time: their ids,
+            // then their frontier bits, each batch in one round trip
             const int32_t lim = min(re, rb + kWarpRow);
-            for (int32_t k = rb; k < lim && !found; k++) {
-                const int32_t x = __ldg(A.nbr + k);
+            for (int32_t k0 = rb; k0 < lim && !found; k0 += kPullBatch) {
+                int32_t x[kPullBatch];
+#pragma unroll
+                for (int r = 0; r < kPullBatch; r++)
+                    x[r] = k0 + r < lim ? __ldg(A.nbr + k0 + r) : -1;
                 uint64_t sm = usm;
-                while (sm) {
+                while (sm && !found) {
                     const int q = __ffsll((long long)sm) - 1;
                     sm &= sm - 1;
-                    if ((__ldcg(F + (size_t)q * p.W + ((uint32_t)x >> 6)) >> (x & 63)) & 1ull) {
-                        found = true;
-                        break;
-                    }
+                    const uint64_t *Fq = F + (size_t)q * p.W;
+                    uint64_t fw[kPullBatch];
+#pragma unroll
+                    for (int r = 0; r < kPullBatch; r++)
+                        fw[r] = x[r] >= 0 ? __ldcg(Fq + ((uint32_t)x[r] >> 6)) : 0ull;
+#pragma unroll
+                    for (int r = 0; r < kPullBatch; r++)
+                        found |= x[r] >= 0 && ((fw[r] >> (x[r] & 63)) & 1ull);
                 }
             }
             pending = !found && re - rb > kWarpRow;
@@ -794,35 +888,90 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     }
 }
 
-// Decide for level j (all CTAs compute the same from the same counters).
-// Returns false when the traversal is over.
-__device__ bool decide_phase(const KParams &p, int j, const Shared &sh) {
+// Level bookkeeping in shared memory, from the device counters of level j
+// (stable while level j runs: its discoveries go to slot (j+1) % 3): the
+// current level becomes the previous one, and level j's frontier of state q
+// is the list range VL[q][vstart[q], vstart[q] + fl[q]).  All loads are
+// issued before the first use (one memory round trip).
+__device__ __forceinline__ void level_advance(const KParams &p, int j, const Shared &sh, bool account) {
+    static_assert(kMaxGroups <= 2 * kThreads && kMaxStates <= kThreads, "one pass of loads");
     const int cs = j % 3;
-    for (int q = threadIdx.x; q < kMaxStates; q += kThreads) sh.fl_prev[q] = sh.fl[q];
-    __syncthreads();
-    if (threadIdx.x < p.S)
-        sh.fl[threadIdx.x] = *(volatile unsigned long long *)&p.c->fl_count[cs][threadIdx.x];
-    for (int g = threadIdx.x; g < p.n_groups; g += kThreads)
-        sh.mfv[g] = __ldcg(p.mf + cs * kMaxGroups + g);
-    __shared__ unsigned long long s_lvl[2];
-    if (threadIdx.x == 0) {
-        s_lvl[0] = *(volatile unsigned long long *)&p.c->lvl_bytes[cs];
-        s_lvl[1] = *(volatile unsigned long long *)&p.c->lvl_edges[cs];
+    const int t = threadIdx.x, g1 = t + kThreads;
+    const unsigned long long fv =
+        t < p.S ? *(volatile unsigned long long *)&p.c->fl_count[cs][t] : 0ull;
+    const unsigned long long m0 = t < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + t) : 0ull;
+    const unsigned long long m1 = g1 < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + g1) : 0ull;
+    unsigned long long lb = 0, le = 0;
+    if (account && t == 0) {
+        lb = *(volatile unsigned long long *)&p.c->lvl_bytes[cs];
+        le = *(volatile unsigned long long *)&p.c->lvl_edges[cs];
     }
     __syncthreads();
+    if (t < kMaxStates) {
+        sh.fl_prev[t] = sh.fl[t];
+        sh.vprev[t] = sh.vstart[t];
+        sh.vstart[t] += (long long)sh.fl[t];
+        sh.fl[t] = fv;
+        sh.vnext[t] = sh.vstart[t] + (long long)fv;
+    }
+    if (t < p.n_groups) sh.mfv[t] = m0;
+    if (g1 < p.n_groups) sh.mfv[g1] = m1;
+    if (t == 0) {
+        sh.lvl[0] = lb;
+        sh.lvl[1] = le;
+    }
+    __syncthreads();
+}
+
+// The same state for a CTA joining at level j from the gate, from what CTA 0
+// published when it released the gate.
+__device__ __forceinline__ void level_join(const KParams &p, int j, const Shared &sh) {
+    const int cs = j % 3;
+    const int t = threadIdx.x, g1 = t + kThreads;
+    const bool in = t < p.S;
+    const unsigned long long fv = in ? *(volatile unsigned long long *)&p.c->fl_count[cs][t] : 0ull;
+    const long long fp = in ? __ldcg(&p.c->pub_flprev[t]) : 0;
+    const long long vp = in ? __ldcg(&p.c->pub_vprev[t]) : 0;
+    const long long vs = in ? __ldcg(&p.c->pub_vstart[t]) : 0;
+    const unsigned long long m0 = t < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + t) : 0ull;
+    const unsigned long long m1 = g1 < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + g1) : 0ull;
+    __syncthreads();
+    if (t < kMaxStates) {
+        sh.fl_prev[t] = (unsigned long long)fp;
+        sh.vprev[t] = vp;
+        sh.vstart[t] = vs;
+        sh.fl[t] = fv;
+        sh.vnext[t] = vs + (long long)fv;
+    }
+    if (t < p.n_groups) sh.mfv[t] = m0;
+    if (g1 < p.n_groups) sh.mfv[g1] = m1;
+    __syncthreads();
+}
+
+constexpr int kPlanStop = 0, kPlanGrid = 1, kPlanSolo = 2;
+// push levels with more edges than this test P before each atomicOr (most
+// of their targets are already visited); smaller ones go straight to it
+constexpr unsigned long long kPrecheckMass = 4096;
+
+// Plans level j from the shared state (every working CTA computes the same):
+// stop when M_j is empty or the level cap is reached; else push or pull per
+// unit (d, q'), and whether the level is small enough for CTA 0 alone.
+// CTA 0 also accumulates the query's statistics (`account`).
+__device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared &sh, bool account) {
+    __shared__ int s_plan;
     long long total = 0;
     for (int q = 0; q < p.S; q++) total += (long long)sh.fl[q];
     const bool expand = total > 0 && (p.max_levels == 0 || j < p.max_levels);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (account && threadIdx.x == 0) {
         p.c->visited += total;
         if (total > 0 && j > 0) p.c->levels = j;
         if (expand) {
             p.c->expanded += total;
-            p.c->push_bytes += (long long)s_lvl[0];
-            p.c->product_edges += (long long)s_lvl[1];
+            p.c->push_bytes += (long long)sh.lvl[0];
+            p.c->product_edges += (long long)sh.lvl[1];
         }
     }
-    if (!expand) return false;
+    if (!expand) return kPlanStop;
     for (int u = threadIdx.x; u < p.n_units; u += kThreads) {
         unsigned long long mass = 0, pairs = 0;
         for (int k = 0; k < sh.ug_count[u]; k++) {
@@ -847,9 +996,13 @@ __device__ bool decide_phase(const KParams &p, int j, const Shared &sh) {
     __syncthreads();
     if (threadIdx.x == 0) {
         long long acc = 0;
+        unsigned long long mass = 0;
         for (int g = 0; g < p.n_groups; g++) {
             sh.gpref[g] = acc;
-            if (sh.tpush[g]) acc += (long long)sh.fl[sh.gq[g]];
+            if (sh.tpush[g]) {
+                acc += (long long)sh.fl[sh.gq[g]];
+                mass += sh.mfv[g];
+            }
         }
         sh.gpref[p.n_groups] = acc;
         long long ra = 0, npush = 0, npull = 0;
@@ -863,13 +1016,140 @@ __device__ bool decide_phase(const KParams &p, int j, const Shared &sh) {
             }
         }
         sh.upref[p.n_units] = ra;
-        if (blockIdx.x == 0) {
+        if (account) {
             p.c->push_units += npush;
             p.c->pull_units += npull;
         }
+        const bool solo = p.solo_mass >= 0 && npull == 0 &&
+                          mass <= (unsigned long long)p.solo_mass && acc <= p.solo_items;
+        s_plan = solo ? kPlanSolo : kPlanGrid;
+        sh.flags[0] = mass > (unsigned long long)kPrecheckMass ? 1 : 0;
     }
     __syncthreads();
-    return true;
+    const int plan = s_plan;
+    __syncthreads();
+    return plan;
+}
+
+// ---------------------------------------------------------------- gate ---
+// While CTA 0 runs levels alone the other CTAs wait at the gate: a word
+// holding (launch epoch << 32) | releases so far.  Every CTA counts the
+// releases it has seen, so a CTA that arrives late still finds its release;
+// the epoch tells this launch's releases from a previous launch's.
+constexpr int kGateLevel = 1;   // join the published level
+constexpr int kGateFinal = 2;   // join the grid-wide answer sweep after the published level
+constexpr int kGateDone = 3;    // the query is finished: exit
+constexpr int kGateError = -1;  // the query failed, or CTA 0 stalled past the limit
+
+// Waits for release number seen + 1 and returns its command; kGateError when
+// the query failed or CTA 0 made no progress (its heartbeat did not change)
+// for the timeout.
+__device__ __forceinline__ int gate_wait(const KParams &p, unsigned &seen) {
+    __shared__ int s_cmd;
+    if (threadIdx.x == 0) {
+        volatile unsigned long long *gp = &p.c->gate;
+        volatile unsigned long long *bp = &p.c->beat;
+        unsigned long long beat = *bp;
+        uint64_t t0 = global_timer_ns();
+        int cmd = kGateError;
+        for (unsigned it = 1;; it++) {
+            const unsigned long long gv = *gp;
+            if ((uint32_t)(gv >> 32) == p.epoch && (uint32_t)gv > seen) {
+                __threadfence();
+                cmd = *(volatile int32_t *)&p.c->gate_cmd;
+                break;
+            }
+            if ((it & 31u) == 0) {
+                if (load_status(p.c) != 0) break;
+                const unsigned long long b = *bp;
+                const uint64_t now = global_timer_ns();
+                if (b != beat) {
+                    beat = b;
+                    t0 = now;
+                } else if (now - t0 > kBarrierTimeoutNs) {
+                    atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_TIMEOUT);
+                    break;
+                }
+            }
+            __nanosleep(128);
+        }
+        s_cmd = cmd;
+    }
+    __syncthreads();
+    const int cmd = s_cmd;
+    __syncthreads();
+    seen++;
+    return cmd;
+}
+
+// CTA 0 (all its threads): publish the state of level j, then release the
+// gate with `cmd`.
+__device__ __forceinline__ void gate_release(const KParams &p, const Shared &sh, unsigned &seen, int cmd,
+                                             int j) {
+    if (cmd != kGateDone) {
+        for (int q = threadIdx.x; q < p.S; q += kThreads) {
+            p.c->pub_vstart[q] = sh.vstart[q];
+            p.c->pub_vprev[q] = sh.vprev[q];
+            p.c->pub_flprev[q] = (long long)sh.fl_prev[q];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *(volatile int32_t *)&p.c->pub_level = j;
+        *(volatile int32_t *)&p.c->gate_cmd = cmd;
+        __threadfence();
+        atomicExch(&p.c->gate, ((unsigned long long)p.epoch << 32) | (unsigned long long)(seen + 1));
+    }
+    seen++;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void heartbeat(const KParams &p) {
+    if (threadIdx.x == 0) atomicAdd(&p.c->beat, 1ull);
+}
+
+// A CTA leaving the grid for the gate has finished with the level it
+// leaves (its counters read, its frontier bits cleared): it says so here.
+__device__ __forceinline__ void park_arrive(const KParams &p) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&p.c->parked, 1ull);
+    }
+}
+
+// CTA 0 (all threads): waits until `expected` parkings have arrived, before
+// it reuses what the parking CTAs were still reading or clearing.  Bounded;
+// false on timeout or a failed query.
+__device__ __forceinline__ bool park_wait(const KParams &p, unsigned long long expected) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned long long *pk = &p.c->parked;
+        int ok = 1;
+        if (*pk < expected) {
+            const uint64_t t0 = global_timer_ns();
+            for (unsigned it = 1; *pk < expected; it++) {
+                if ((it & 63u) == 0) {
+                    if (load_status(p.c) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_timer_ns() - t0 > kBarrierTimeoutNs) {
+                        atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    const int ok = s_ok;
+    __syncthreads();
+    return ok != 0;
 }
 
 // F x P with ordered compaction (two phases around one barrier).
@@ -898,6 +1178,8 @@ __device__ void final_phase(const KParams &p, long long *s_tmp) {
     if (threadIdx.x == 0) p.fin_sums[blockIdx.x] = *s_tmp;
 }
 
+// Second pass: each CTA writes its range's answer vertices after the counts
+// of the CTAs before it, and clears the final states' P words it read.
 __device__ void final_write(const KParams &p, long long *s_tmp) {
     const int64_t W = p.W;
     const int64_t per = (W + gridDim.x - 1) / gridDim.x;
@@ -934,7 +1216,6 @@ __device__ void final_write(const KParams &p, long long *s_tmp) {
     __syncthreads();
     long long run = *s_tmp;
     __syncthreads();
-    if (!p.out_list) return;
     const unsigned lane = lane_id();
     for (int64_t base = w0; base < w1; base += kThreads) {
         const int64_t wi = base + threadIdx.x;
@@ -944,9 +1225,13 @@ __device__ void final_write(const KParams &p, long long *s_tmp) {
             while (fm) {
                 const int q = __ffsll((long long)fm) - 1;
                 fm &= fm - 1;
-                r |= __ldcg(p.P + (size_t)q * W + wi);
+                uint64_t *Pw = p.P + (size_t)q * W + wi;
+                const uint64_t v = __ldcg(Pw);
+                if (v) *Pw = 0;
+                r |= v;
             }
         }
+        if (!p.out_list) continue;  // CTA-uniform
         const int32_t c = __popcll(r);
         int32_t incl = c;
         for (int o = 1; o < 32; o <<= 1) {
@@ -977,14 +1262,225 @@ __device__ void final_write(const KParams &p, long long *s_tmp) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) rpq_query_kernel(KParams p) {
+// Frontier bits of levels j-1 and j cleared on CTA `cta` of `ncta`: the
+// list ranges [vprev, vstart) in slot (j-1) % 3 and [vstart, vnext) in slot
+// j % 3.  Loads go in batches of four ahead of their stores.
+__device__ __forceinline__ void clear_frontier_bits(const KParams &p, const Shared &sh, int j, int cta, int ncta) {
+    const long long first = (long long)cta * kThreads + threadIdx.x;
+    const long long stride = (long long)ncta * kThreads;
+    for (int q = 0; q < p.S; q++) {
+        const int32_t *lst = p.VL + (size_t)q * p.n;
+        const long long b = sh.vprev[q], m = sh.vstart[q], e = sh.vnext[q];
+        uint64_t *Fa = p.F[(j + 2) % 3] + (size_t)q * p.W;
+        uint64_t *Fb = p.F[j % 3] + (size_t)q * p.W;
+        for (long long i0 = b + first; i0 < e; i0 += 4 * stride) {
+            int32_t v[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const long long i = i0 + r * stride;
+                v[r] = i < e ? __ldcg(lst + i) : -1;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+                if (v[r] >= 0) (i0 + r * stride < m ? Fa : Fb)[(uint32_t)v[r] >> 6] = 0;
+        }
+    }
+}
+
+// CTA 0: sets the frontier bits of level j (list range [vstart, vnext)) in
+// slot j % 3, for a level that the whole grid is about to run.
+__device__ __forceinline__ void set_frontier_bits(const KParams &p, const Shared &sh, int j) {
+    for (int q = 0; q < p.S; q++) {
+        const int32_t *lst = p.VL + (size_t)q * p.n;
+        uint64_t *Fq = p.F[j % 3] + (size_t)q * p.W;
+        for (long long i = sh.vstart[q] + threadIdx.x; i < sh.vnext[q]; i += kThreads) {
+            const int32_t v = __ldcg(lst + i);
+            atomicOr((unsigned long long *)(Fq + ((uint32_t)v >> 6)), 1ull << (v & 63));
+        }
+    }
+}
+
+// Restores the all-zero P and F on CTA `cta` of `ncta` after a query whose
+// last level is j: P rows (all states, or only the non-final ones when the
+// answer sweep cleared the final rows), through the lists when they are
+// short, densely over this CTA's word range otherwise; and, when the last
+// levels kept frontier bits (`f_live`), those bits.
+__device__ void clear_state(const KParams &p, const Shared &sh, bool finals_too, bool f_live,
+                            int j, int cta, int ncta) {
+    const int64_t W = p.W;
+    const int64_t per = (W + ncta - 1) / ncta;
+    const int64_t w0 = (int64_t)min((long long)W, (long long)cta * per);
+    const int64_t w1 = (int64_t)min((long long)W, (long long)(w0 + per));
+    const long long first = (long long)cta * kThreads + threadIdx.x;
+    const long long stride = (long long)ncta * kThreads;
+    for (int q = 0; q < p.S; q++) {
+        if (!finals_too && ((p.final_mask >> q) & 1ull)) continue;
+        const long long vend = sh.vstart[q] + (long long)sh.fl[q];
+        const int32_t *lst = p.VL + (size_t)q * p.n;
+        uint64_t *Pq = p.P + (size_t)q * W;
+        if (vend * 8 < W) {
+            for (long long i0 = first; i0 < vend; i0 += 4 * stride) {
+                int32_t v[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const long long i = i0 + r * stride;
+                    v[r] = i < vend ? __ldcg(lst + i) : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+                    if (v[r] >= 0) Pq[(uint32_t)v[r] >> 6] = 0;
+            }
+        } else {
+            for (int64_t wi = w0 + threadIdx.x; wi < w1; wi += kThreads) Pq[wi] = 0;
+        }
+    }
+    if (f_live) clear_frontier_bits(p, sh, j, cta, ncta);
+}
+
+constexpr int kSoloAnswer = kGather;    // answer entries CTA 0 sorts in shared memory
+constexpr long long kSoloClear = 4096;  // visited pairs CTA 0 clears through the lists
+
+// Whether CTA 0 alone finishes the query: a list answer of at most
+// kSoloAnswer entries (before removing duplicates across final states) and
+// at most kSoloClear visited pairs.  Same result on every CTA.
+__device__ bool solo_finish(const KParams &p, const Shared &sh) {
+    if (p.out_bits) return false;
+    long long t = 0, v = 0;
+    for (int q = 0; q < p.S; q++) {
+        const long long e = sh.vstart[q] + (long long)sh.fl[q];
+        v += e;
+        if ((p.final_mask >> q) & 1ull) t += e;
+    }
+    return t <= kSoloAnswer && v <= kSoloClear;
+}
+
+// CTA 0 alone, after a query whose last level is j: one pass over every
+// visited list clears P (and the kept frontier bits) and gathers the final
+// states' vertices; the answer is their union, sorted by a bitonic network
+// in shared memory with duplicates dropped.
+__device__ void solo_answer(const KParams &p, const Shared &sh, bool f_live, int j) {
+    int32_t *buf = sh.gbuf_k;
+    __shared__ long long s_off[kMaxStates + 1];  // list prefix over all states
+    __shared__ long long s_fo[kMaxStates + 1];   // list prefix over final states
+    __shared__ int s_wc[kWarps];
+    if (threadIdx.x == 0) {
+        long long t = 0, f = 0;
+        for (int q = 0; q < p.S; q++) {
+            s_off[q] = t;
+            s_fo[q] = f;
+            const long long e = sh.vstart[q] + (long long)sh.fl[q];
+            t += e;
+            if ((p.final_mask >> q) & 1ull) f += e;
+        }
+        s_off[p.S] = t;
+        s_fo[p.S] = f;
+    }
+    __syncthreads();
+    const long long V = s_off[p.S];
+    const int T = (int)s_fo[p.S];
+    uint64_t *Fa = p.F[(j + 2) % 3], *Fb = p.F[j % 3];
+    for (long long base = 0; base < V; base += 4 * kThreads) {
+        int32_t v[4];
+        int qq[4];
+        long long ii[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const long long idx = base + r * kThreads + threadIdx.x;
+            qq[r] = -1;
+            ii[r] = 0;
+            v[r] = 0;
+            if (idx < V) {
+                int q = 0;
+                while (q + 1 < p.S && s_off[q + 1] <= idx) q++;
+                qq[r] = q;
+                ii[r] = idx - s_off[q];
+                v[r] = __ldcg(p.VL + (size_t)q * p.n + ii[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int q = qq[r];
+            if (q < 0) continue;
+            const uint32_t wi = (uint32_t)v[r] >> 6;
+            p.P[(size_t)q * p.W + wi] = 0;
+            if (f_live && ii[r] >= sh.vprev[q])
+                (ii[r] < sh.vstart[q] ? Fa : Fb)[(size_t)q * p.W + wi] = 0;
+            if ((p.final_mask >> q) & 1ull) buf[s_fo[q] + ii[r]] = v[r];
+        }
+    }
+    int n2 = 32;
+    while (n2 < T) n2 <<= 1;
+    for (int i = T + threadIdx.x; i < n2; i += kThreads) buf[i] = INT32_MAX;
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += kThreads) {
+                const int x = i ^ jj;
+                if (x > i) {
+                    const int32_t a = buf[i], b = buf[x];
+                    if ((a > b) == ((i & k) == 0)) {
+                        buf[i] = b;
+                        buf[x] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    long long run = 0;
+    for (int base = 0; base < n2; base += kThreads) {
+        const int i = base + threadIdx.x;
+        const int32_t v = i < n2 ? buf[i] : INT32_MAX;
+        const bool keep = i < n2 && v != INT32_MAX && (i == 0 || buf[i - 1] != v);
+        const unsigned bm = __ballot_sync(kFull, keep);
+        if (lane == 0) s_wc[warp] = __popc(bm);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int w = 0; w < kWarps; w++) {
+            const int c = s_wc[w];
+            if (w < warp) before += c;
+            tot += c;
+        }
+        const long long pos = run + before + __popc(bm & lanemask_lt());
+        if (keep && p.out_list && pos < p.capacity) p.out_list[pos] = v;
+        run += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) p.c->answer_count = run;
+}
+
+// CTA 0, thread 0, at the end of a successful query: the summary to the
+// host-mapped result (every field is thread 0's own earlier write).
+__device__ __forceinline__ void write_result(const KParams &p) {
+    if (!p.result || threadIdx.x != 0) return;
+    const volatile Counters *c = p.c;
+    QueryResult *r = p.result;
+    r->levels = c->levels;
+    r->visited = c->visited;
+    r->expanded = c->expanded;
+    r->product_edges = c->product_edges;
+    r->push_bytes = c->push_bytes;
+    r->push_units = c->push_units;
+    r->pull_units = c->pull_units;
+    r->answer_count = c->answer_count;
+    r->epoch = p.epoch;  // the host reads the summary after the stream has synchronised
+}
+
+__global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_constant__ KParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int32_t s_gsf[kMaxStates + 1];
     __shared__ long long s_claim;
     __shared__ unsigned long long s_acc[2];
-    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+    const bool lead = blockIdx.x == 0;
+    if (p.trace && lead && threadIdx.x == 0)
         p.trace[(size_t)(p.trace_cap) * kTraceFields + 0] = global_timer_ns();
-    Shared sh = carve(p, smem);
+    // the layout's pointers live in shared memory, not in 30 registers
+    __shared__ Shared s_layout;
+    if (threadIdx.x == 0) s_layout = carve(p, smem);
+    __syncthreads();
+    const Shared &sh = s_layout;
     load_tables(p, sh);
     if (threadIdx.x <= p.S) {
         int lo = 0, hi = p.n_groups;  // groups are sorted by source state
@@ -996,22 +1492,24 @@ __global__ void __launch_bounds__(kThreads) rpq_query_kernel(KParams p) {
     }
     if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
     __syncthreads();
-    // prologue: P = F_0 = Q_S x {v_s}; F_1 = F_2 = 0; counters of all slots
-    // cleared; level 0 lists and rows seeded by warp 0 of CTA 0
-    const uint32_t swi = (uint32_t)p.source >> 6;
-    const uint64_t sbit = 1ull << (p.source & 63);
-    const size_t words = (size_t)p.S * p.W;
-    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < words;
-         i += (size_t)gridDim.x * kThreads) {
-        const int q = (int)(i / p.W);
-        const uint64_t v =
-            ((uint32_t)(i - (size_t)q * p.W) == swi && ((p.start_mask >> q) & 1ull)) ? sbit : 0ull;
-        p.P[i] = v;
-        p.F[0][i] = v;
-        p.F[1][i] = 0;
-        p.F[2][i] = 0;
+    if (p.clear_first) {
+        const size_t words = (size_t)p.S * p.W;
+        for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < words;
+             i += (size_t)gridDim.x * kThreads) {
+            p.P[i] = 0;
+            p.F[0][i] = 0;
+            p.F[1][i] = 0;
+            p.F[2][i] = 0;
+        }
+        if (!grid_barrier(p.c)) return;
     }
-    if (blockIdx.x == 0) {
+    unsigned seen = 0;   // gate releases seen (the same count on every CTA)
+    bool grid = false;   // the current level runs on the whole grid
+    bool from_gate_final = false;
+    int j = 0, plan = kPlanStop;
+    if (lead) {
+        // prologue on CTA 0: counters of all slots cleared; P = F_0 = Q_S x {v_s}
+        // with the level-0 lists, edge mass and long rows of every start state
         for (int i = threadIdx.x; i < 3 * kMaxGroups; i += kThreads) p.mf[i] = 0;
         if (threadIdx.x == 0) {
             Counters *c = p.c;
@@ -1022,16 +1520,20 @@ __global__ void __launch_bounds__(kThreads) rpq_query_kernel(KParams p) {
             }
             c->levels = c->visited = c->expanded = c->product_edges = c->push_bytes = 0;
             c->push_units = c->pull_units = c->answer_count = 0;
+            c->parked = 0;
         }
         __syncthreads();
         if (threadIdx.x < 32) {
-            // the bits of F_0 and P were set above; this adds the level-0
-            // lists, edge mass and long rows of every start state
-            LevelCtx L0{0, p.FL[0], p.F[0], p.rows[0], p.cmap[0], s_acc};
+            // CTA 0 starts alone: like every solo level, no frontier bits
+            LevelCtx L0{0, p.VL, sh.vnext, nullptr, p.rows[0], p.cmap[0], s_acc};
+            const uint32_t swi = (uint32_t)p.source >> 6;
+            const uint64_t sbit = 1ull << (p.source & 63);
             uint64_t sm = p.start_mask;
             while (sm) {
                 const int q = __ffsll((long long)sm) - 1;
                 sm &= sm - 1;
+                if (lane_id() == 0)
+                    atomicOr((unsigned long long *)(p.P + (size_t)q * p.W + swi), sbit);
                 warp_discover(p, sh, s_gsf, L0, lane_id() == 0, q, p.source);
             }
             __syncwarp();
@@ -1045,33 +1547,106 @@ __global__ void __launch_bounds__(kThreads) rpq_query_kernel(KParams p) {
                 sh.s_mf[g] = 0;
             }
         }
+        __syncthreads();
+        if (p.trace && threadIdx.x == 0)
+            p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
+        level_advance(p, 0, sh, true);
+        plan = level_plan(p, 0, sh, true);
     }
-    if (!grid_barrier(p.c)) return;
-    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
-        p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
-    for (int j = 0;; j++) {
-        const bool more = decide_phase(p, j, sh);
+    bool prev_grid = false;  // level j-1 ran on the grid (its frontier bits exist)
+    unsigned long long parked_expected = 0;  // CTA 0: parkings so far
+    bool park_pending = false;               // CTA 0: the last parking may be incomplete
+    for (;;) {
+        if (!lead && !grid) {
+            // parked while CTA 0 runs levels alone
+            const int cmd = gate_wait(p, seen);
+            if (cmd != kGateLevel && cmd != kGateFinal) return;
+            j = *(volatile int32_t *)&p.c->pub_level;
+            level_join(p, j, sh);
+            grid = true;
+            prev_grid = false;
+            if (cmd == kGateFinal) {
+                from_gate_final = true;
+                break;
+            }
+            plan = level_plan(p, j, sh, false);
+        }
+        if (plan == kPlanStop) break;
+        if (grid && plan == kPlanSolo) {
+            // solo levels neither set nor clear frontier bits: the grid clears
+            // those of levels j-1 and j now.  Each other CTA then parks;
+            // CTA 0 runs level j at once and waits for the parkings only
+            // before it recycles level j's counter slot or wakes the grid
+            clear_frontier_bits(p, sh, j, (int)blockIdx.x, (int)gridDim.x);
+            grid = false;
+            prev_grid = false;
+            if (!lead) {
+                park_arrive(p);
+                continue;  // park
+            }
+            parked_expected += gridDim.x - 1;
+            park_pending = true;
+        } else if (!grid && plan == kPlanGrid) {
+            if (park_pending && !park_wait(p, parked_expected)) return;
+            park_pending = false;
+            set_frontier_bits(p, sh, j);  // level j may pull: its frontier needs its bits
+            gate_release(p, sh, seen, kGateLevel, j);
+            grid = true;
+        } else if (!grid && park_pending) {
+            // the second solo level after a parking recycles the counter slot
+            // of the level the parking CTAs last read
+            if (!park_wait(p, parked_expected)) return;
+            park_pending = false;
+        }
         trace_put(p, j, 0, global_timer_ns());
-        if (p.trace && blockIdx.x == 0 && threadIdx.x == 0 && j < p.trace_cap) {
+        if (p.trace && lead && threadIdx.x == 0 && j < p.trace_cap) {
             unsigned long long tot = 0, npull = 0;
             for (int q = 0; q < p.S; q++) tot += sh.fl[q];
             for (int u = 0; u < p.n_units; u++) npull += sh.upull[u];
             p.trace[(size_t)j * kTraceFields + 3] = tot;
-            p.trace[(size_t)j * kTraceFields + 4] = more ? (unsigned long long)p.n_units - npull : 0;
-            p.trace[(size_t)j * kTraceFields + 5] = more ? npull : 0;
+            p.trace[(size_t)j * kTraceFields + 4] = (unsigned long long)p.n_units - npull;
+            p.trace[(size_t)j * kTraceFields + 5] = npull;
+            p.trace[(size_t)j * kTraceFields + 6] = grid ? 1 : 0;
         }
-        if (!more) break;
-        expand_phase(p, j, sh, s_gsf, &s_claim, s_acc);
+        expand_phase(p, j, sh, s_gsf, &s_claim, s_acc, grid ? (int)blockIdx.x : 0,
+                     grid ? (int)gridDim.x : 1, grid, grid && prev_grid);
+        prev_grid = grid;
         trace_put(p, j, 1, global_timer_ns());
-        if (!grid_barrier(p.c)) return;
+        if (grid) {
+            if (!grid_barrier(p.c)) return;
+        } else {
+            __syncthreads();
+            heartbeat(p);
+            if (load_status(p.c) != 0) return;
+        }
         trace_put(p, j, 2, global_timer_ns());
+        j++;
+        level_advance(p, j, sh, lead);
+        plan = level_plan(p, j, sh, lead);
     }
-    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+    if (p.trace && lead && threadIdx.x == 0)
         p.trace[(size_t)(p.trace_cap) * kTraceFields + 2] = global_timer_ns();
-    final_phase(p, &s_claim);
-    if (!grid_barrier(p.c)) return;
-    final_write(p, &s_claim);
-    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+    // frontier bits exist only when the last levels ran on the grid
+    const bool f_live = grid && !from_gate_final;
+    bool solo_end = false;
+    if (!from_gate_final && solo_finish(p, sh)) {
+        if (!lead) return;
+        if (!grid) gate_release(p, sh, seen, kGateDone, j);
+        solo_answer(p, sh, f_live, j);
+        __syncthreads();
+        solo_end = true;
+    } else if (!grid) {
+        gate_release(p, sh, seen, kGateFinal, j);
+        grid = true;
+    }
+    if (!solo_end) {
+        final_phase(p, &s_claim);
+        if (!grid_barrier(p.c)) return;
+        final_write(p, &s_claim);
+        clear_state(p, sh, false, f_live, j, (int)blockIdx.x, (int)gridDim.x);
+    }
+    if (lead) write_result(p);
+    if (p.trace && lead && threadIdx.x == 0)
         p.trace[(size_t)(p.trace_cap) * kTraceFields + 3] = global_timer_ns();
 }
 
@@ -1081,9 +1656,12 @@ struct QueryWorkspace : WorkspaceBase {
     int S_cap = 0;
     long long row_cap = 0, chunk_cap = 0;
     int32_t n = 0, W = 0;
-    DevBuf P, F[3], FL[3], rows[3], cmap[3], mf, fin, ctr, tables, out_list, trace;
+    DevBuf P, F[3], VL, rows[3], cmap[3], mf, fin, ctr, tables, out_list, trace;
     void *staging = nullptr;  // pinned host: tables upload + counters download
     size_t staging_bytes = 0;
+    QueryResult *result_dev = nullptr;  // device address of the summary slot of staging
+    uint32_t epoch = 0;   // launches so far (tags the kernel's gate word and the summary)
+    bool dirty = false;   // a failed launch may have left P / F non-zero
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     ~QueryWorkspace() override {
         if (staging) cudaFreeHost(staging);
@@ -1093,6 +1671,8 @@ struct QueryWorkspace : WorkspaceBase {
 };
 
 constexpr size_t kTablesBytes = 256 * 1024;
+// staging: tables | counters (read back after a failure) | summary
+constexpr size_t kResultOffset = (kTablesBytes + sizeof(Counters) + 63) & ~size_t(63);
 
 // Grid of the persistent kernel: every SM holds the same number of CTAs
 // (cooperative launch requires all of them resident).  Computed per device
@@ -1147,15 +1727,22 @@ rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long
     ws->W = (int32_t)W;
     bool ok = ws->P.alloc(bits) && ws->mf.alloc(sizeof(unsigned long long) * 3 * kMaxGroups) &&
               ws->fin.alloc(sizeof(long long) * 152 * 64) && ws->ctr.alloc(sizeof(Counters)) &&
-              ws->tables.alloc(kTablesBytes) && ws->out_list.alloc(sizeof(int32_t) * (size_t)g->n);
+              ws->tables.alloc(kTablesBytes) && ws->out_list.alloc(sizeof(int32_t) * (size_t)g->n) &&
+              ws->VL.alloc(fl);
     for (int k = 0; k < 3 && ok; k++)
-        ok = ws->F[k].alloc(bits) && ws->FL[k].alloc(fl) &&
-             ws->rows[k].alloc(sizeof(Row) * (size_t)row_cap) &&
+        ok = ws->F[k].alloc(bits) && ws->rows[k].alloc(sizeof(Row) * (size_t)row_cap) &&
              ws->cmap[k].alloc(sizeof(int32_t) * (size_t)chunk_cap);
     if (!ok) return fail(RPQ_ERR_OOM, "query workspace (%d states)", S_cap);
+    // the kernel expects P and F all-zero on entry and leaves them so
     RPQ_CUDA_TRY(cudaMemset(ws->ctr.p, 0, sizeof(Counters)));
-    ws->staging_bytes = kTablesBytes + sizeof(Counters) + 64;
-    RPQ_CUDA_TRY(cudaMallocHost(&ws->staging, ws->staging_bytes));
+    RPQ_CUDA_TRY(cudaMemset(ws->P.p, 0, bits));
+    for (int k = 0; k < 3; k++) RPQ_CUDA_TRY(cudaMemset(ws->F[k].p, 0, bits));
+    ws->staging_bytes = kResultOffset + sizeof(QueryResult);
+    RPQ_CUDA_TRY(cudaHostAlloc(&ws->staging, ws->staging_bytes, cudaHostAllocMapped));
+    memset(ws->staging, 0, ws->staging_bytes);
+    void *rd = nullptr;
+    RPQ_CUDA_TRY(cudaHostGetDevicePointer(&rd, static_cast<uint8_t *>(ws->staging) + kResultOffset, 0));
+    ws->result_dev = static_cast<QueryResult *>(rd);
     RPQ_CUDA_TRY(cudaEventCreate(&ws->ev0));
     RPQ_CUDA_TRY(cudaEventCreate(&ws->ev1));
     return RPQ_OK;
@@ -1264,7 +1851,8 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
 
 // Appends one JSON line per query: the kernel's phase times and, per level,
 // block 0's timestamps (ns, relative to the kernel start) with the frontier
-// size and the number of push / pull units.
+// size, the number of push / pull units and whether the level ran on the
+// whole grid (1) or on CTA 0 alone (0).
 void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int levels,
                  cudaStream_t st) {
     std::vector<unsigned long long> h((size_t)kTraceFields * levels), gs(kTraceFields);
@@ -1285,11 +1873,59 @@ void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int le
     for (int j = 0; j < levels; j++) {
         const unsigned long long *r = &h[(size_t)j * kTraceFields];
         if (r[0] == 0) break;
-        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu]", j ? ", " : "", rel(r[0]), rel(r[1]),
-                rel(r[2]), r[3], r[4], r[5]);
+        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu, %llu]", j ? ", " : "", rel(r[0]),
+                rel(r[1]), rel(r[2]), r[3], r[4], r[5], r[6]);
     }
     fprintf(f, "]}\n");
     fclose(f);
+}
+
+// Packs the tables at 16-byte aligned offsets into dst (cap bytes), writing
+// the five offsets; returns the packed size, which may exceed cap (then
+// nothing past cap is written).
+size_t pack_tables(const Tables &t, uint8_t *dst, size_t cap, int32_t off[5]) {
+    size_t o = 0;
+    int k = 0;
+    auto put = [&](const void *src, size_t bytes) {
+        o = (o + 15) & ~size_t(15);
+        off[k++] = (int32_t)o;
+        if (bytes && o + bytes <= cap) memcpy(dst + o, src, bytes);
+        o += bytes;
+    };
+    put(t.groups.data(), sizeof(QGroup) * t.groups.size());
+    put(t.units.data(), sizeof(QUnit) * t.units.size());
+    put(t.t_unit.data(), sizeof(int32_t) * t.t_unit.size());
+    put(t.t_state.data(), sizeof(int32_t) * t.t_state.size());
+    put(t.u_group.data(), sizeof(int32_t) * t.u_group.size());
+    return (o + 15) & ~size_t(15);
+}
+
+// Tables into the launch parameters when they fit, else into `dev` (a
+// device buffer of cap bytes) through `staging` (pinned host) on `st`.
+rpq_status place_tables(const Tables &t, KParams &p, uint8_t *staging, uint8_t *dev, size_t cap,
+                        cudaStream_t st, size_t *bytes) {
+    int32_t off[5];
+    size_t n = pack_tables(t, p.tab, kInlineTables, off);
+    *bytes = n;
+    if (n <= (size_t)kInlineTables) {
+        p.tab_inline = 1;
+        p.o_groups = off[0];
+        p.o_units = off[1];
+        p.o_tu = off[2];
+        p.o_ts = off[3];
+        p.o_ug = off[4];
+        return RPQ_OK;
+    }
+    if (n > cap) return fail(RPQ_ERR_INVALID, "automaton tables too large (%zu bytes)", n);
+    pack_tables(t, staging, cap, off);
+    RPQ_CUDA_TRY(cudaMemcpyAsync(dev, staging, n, cudaMemcpyHostToDevice, st));
+    p.tab_inline = 0;
+    p.groups = reinterpret_cast<const QGroup *>(dev + off[0]);
+    p.units = reinterpret_cast<const QUnit *>(dev + off[1]);
+    p.t_unit = reinterpret_cast<const int32_t *>(dev + off[2]);
+    p.t_state = reinterpret_cast<const int32_t *>(dev + off[3]);
+    p.u_group = reinterpret_cast<const int32_t *>(dev + off[4]);
+    return RPQ_OK;
 }
 
 float env_float(const char *name, float dflt) {
@@ -1325,31 +1961,14 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     if (s != RPQ_OK) return s;
     std::unique_ptr<QueryWorkspace> ws = ws_acquire(g, a.S, t.row_need, t.chunk_need, &s);
     if (!ws) return s;
-    // upload tables
     uint8_t *hs = static_cast<uint8_t *>(ws->staging);
-    size_t off = 0;
-    auto put = [&](const void *src, size_t bytes) {
-        off = (off + 15) & ~size_t(15);
-        size_t at = off;
-        if (bytes && src && at + bytes <= kTablesBytes) memcpy(hs + at, src, bytes);
-        off += bytes;
-        return at;
-    };
-    const size_t o_groups = put(t.groups.data(), sizeof(QGroup) * t.groups.size());
-    const size_t o_units = put(t.units.data(), sizeof(QUnit) * t.units.size());
-    const size_t o_tu = put(t.t_unit.data(), sizeof(int32_t) * t.t_unit.size());
-    const size_t o_ts = put(t.t_state.data(), sizeof(int32_t) * t.t_state.size());
-    const size_t o_ug = put(t.u_group.data(), sizeof(int32_t) * t.u_group.size());
-    off = (off + 15) & ~size_t(15);
-    if (off > kTablesBytes) {
-        ws_release(g, std::move(ws));
-        return fail(RPQ_ERR_INVALID, "automaton tables too large");
-    }
-    RPQ_CUDA_TRY(cudaMemcpyAsync(ws->tables.p, hs, std::max<size_t>(off, 16),
-                                 cudaMemcpyHostToDevice, st));
-    uint8_t *dt = ws->tables.as<uint8_t>();
-
     KParams p{};
+    size_t tab_bytes = 0;
+    s = place_tables(t, p, hs, ws->tables.as<uint8_t>(), kTablesBytes, st, &tab_bytes);
+    if (s != RPQ_OK) {
+        ws_release(g, std::move(ws));
+        return s;
+    }
     p.adj = g->d_adj.as<DevAdj>();
     p.n = g->n;
     p.W = ws->W;
@@ -1364,15 +1983,16 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     p.final_mask = a.final_mask;
     p.alpha = env_float("RPQ_PULL_ALPHA", g->pull_alpha);
     p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
-    p.groups = reinterpret_cast<const QGroup *>(dt + o_groups);
-    p.units = reinterpret_cast<const QUnit *>(dt + o_units);
-    p.t_unit = reinterpret_cast<const int32_t *>(dt + o_tu);
-    p.t_state = reinterpret_cast<const int32_t *>(dt + o_ts);
-    p.u_group = reinterpret_cast<const int32_t *>(dt + o_ug);
+    p.solo_mass = (int32_t)env_float("RPQ_SOLO_MASS", (float)g->solo_mass);
+    p.solo_items = (int32_t)env_float("RPQ_SOLO_ITEMS", (float)g->solo_items);
+    p.epoch = ++ws->epoch;
+    p.clear_first = ws->dirty ? 1 : 0;
+    QueryResult *hr = reinterpret_cast<QueryResult *>(hs + kResultOffset);
+    p.result = ws->result_dev;
     p.P = ws->P.as<uint64_t>();
+    p.VL = ws->VL.as<int32_t>();
     for (int k = 0; k < 3; k++) {
         p.F[k] = ws->F[k].as<uint64_t>();
-        p.FL[k] = ws->FL[k].as<int32_t>();
         p.rows[k] = ws->rows[k].as<Row>();
         p.cmap[k] = ws->cmap[k].as<int32_t>();
     }
@@ -1412,36 +2032,40 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     }
     if (grid > 152 * 64) grid = 152 * 64;
     if (grid_div > 1) grid = std::max(1, grid / grid_div);
-    RPQ_CUDA_TRY(cudaMemsetAsync(&p.c->status, 0, sizeof(int32_t), st));
     const bool timed = stats != nullptr;
     if (timed) RPQ_CUDA_TRY(cudaEventRecord(ws->ev0, st));
     void *args[] = {&p};
     RPQ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)rpq_query_kernel, dim3(grid),
                                              dim3(kThreads), args, smem, st));
     if (timed) RPQ_CUDA_TRY(cudaEventRecord(ws->ev1, st));
-    Counters *hc = reinterpret_cast<Counters *>(hs + kTablesBytes);
-    RPQ_CUDA_TRY(cudaMemcpyAsync(hc, ws->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hc->status != 0) {
+    if (*(volatile uint32_t *)&hr->epoch != p.epoch) {
+        // no summary: the traversal gave up.  It leaves the barrier counters
+        // mid-way and P / F not cleared: read the status, reset the
+        // counters, clear P / F on next use
+        Counters *hc = reinterpret_cast<Counters *>(hs + kTablesBytes);
+        RPQ_CUDA_TRY(cudaMemcpyAsync(hc, ws->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         cudaMemsetAsync(ws->ctr.p, 0, sizeof(Counters), st);
-        cudaStreamSynchronize(st);
-        const rpq_status e = (rpq_status)hc->status;
+        RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+        ws->dirty = true;
+        const rpq_status e = hc->status != 0 ? (rpq_status)hc->status : RPQ_ERR_CUDA;
         ws_release(g, std::move(ws));
         return fail(e, "device traversal failed (status %d)", (int)e);
     }
-    *count = hc->answer_count;
+    ws->dirty = false;
+    *count = hr->answer_count;
     const bool copy_list = out_host_list && !out_list_dev && *count <= capacity && *count > 0;
     if (stats) {
-        stats->h2d_bytes = (int64_t)std::max<size_t>(off, 16);
-        stats->d2h_bytes = (int64_t)sizeof(Counters) + (copy_list ? 4 * *count : 0);
-        stats->levels = hc->levels;
-        stats->visited_pairs = hc->visited;
-        stats->expanded_pairs = hc->expanded;
-        stats->product_edges = hc->product_edges;
-        stats->push_bytes = hc->push_bytes;
-        stats->answer_count = hc->answer_count;
-        stats->push_unit_levels = hc->push_units;
-        stats->pull_unit_levels = hc->pull_units;
+        stats->h2d_bytes = (int64_t)tab_bytes;
+        stats->d2h_bytes = (int64_t)sizeof(QueryResult) + (copy_list ? 4 * *count : 0);
+        stats->levels = hr->levels;
+        stats->visited_pairs = hr->visited;
+        stats->expanded_pairs = hr->expanded;
+        stats->product_edges = hr->product_edges;
+        stats->push_bytes = hr->push_bytes;
+        stats->answer_count = hr->answer_count;
+        stats->push_unit_levels = hr->push_units;
+        stats->pull_unit_levels = hr->pull_units;
         float ms = -1.0f;
         if (cudaEventElapsedTime(&ms, ws->ev0, ws->ev1) != cudaSuccess) ms = -1.0f;
         stats->device_ms = ms;
@@ -1453,7 +2077,7 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     }
     if (trace_path)
         write_trace(trace_path, ws.get(), a.S, source,
-                    (int)std::min<long long>(hc->levels + 2, kTraceLevels), st);
+                    (int)std::min<long long>(hr->levels + 2, kTraceLevels), st);
     ws_release(g, std::move(ws));
     return RPQ_OK;
 }
@@ -1526,11 +2150,13 @@ static __device__ __align__(256) unsigned char rpq_noalloc_scratch[RPQ_NOALLOC_S
 namespace rpq {
 namespace {
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[64];  // device address of the scratch, per device
+void *g_noalloc_ptr[64];      // device address of the scratch, per device
+uint32_t g_noalloc_epoch[64]; // launches on the scratch, per device
 
 // Device address of the scratch on `device` (which must be current), looked
 // up once per device; the barrier counters are cleared on that first call.
-rpq_status noalloc_scratch(int device, void **out) {
+// Also hands out the launch's epoch.
+rpq_status noalloc_scratch(int device, void **out, uint32_t *epoch) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (device < 0 || device >= 64) return fail(RPQ_ERR_CUDA, "device id %d", device);
     if (!g_noalloc_ptr[device]) {
@@ -1542,6 +2168,7 @@ rpq_status noalloc_scratch(int device, void **out) {
         g_noalloc_ptr[device] = ptr;
     }
     *out = g_noalloc_ptr[device];
+    *epoch = ++g_noalloc_epoch[device];
     return RPQ_OK;
 }
 }  // namespace
@@ -1572,7 +2199,7 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     rpq_status s = build_tables(g, a, &t);
     if (s != RPQ_OK) return s;
 
-    // scratch layout: counters | mf | per-CTA sums | tables | P | F[3] | FL[3] | rows[3] | cmap[3]
+    // scratch layout: counters | mf | per-CTA sums | tables | P | F[3] | VL | rows[3] | cmap[3]
     const int64_t W = ((int64_t)g->n + 63) / 64;
     std::vector<uint8_t> host_tables;
     size_t toff = 0;
@@ -1603,9 +2230,9 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     const size_t bits = sizeof(uint64_t) * (size_t)a.S * W;
     const size_t fl = sizeof(int32_t) * (size_t)a.S * g->n;
     const size_t x_P = take(bits);
-    size_t x_F[3], x_FL[3], x_rows[3], x_cmap[3];
+    size_t x_F[3], x_rows[3], x_cmap[3];
     for (int k = 0; k < 3; k++) x_F[k] = take(bits);
-    for (int k = 0; k < 3; k++) x_FL[k] = take(fl);
+    const size_t x_VL = take(fl);
     for (int k = 0; k < 3; k++) x_rows[k] = take(sizeof(Row) * (size_t)t.row_need);
     for (int k = 0; k < 3; k++) x_cmap[k] = take(sizeof(int32_t) * (size_t)t.chunk_need);
     if (off > RPQ_NOALLOC_SCRATCH_BYTES)
@@ -1614,7 +2241,8 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
                     "(use rpq_query)",
                     off, (unsigned long long)RPQ_NOALLOC_SCRATCH_BYTES);
     void *base_v = nullptr;
-    s = noalloc_scratch(dev, &base_v);
+    uint32_t epoch = 0;
+    s = noalloc_scratch(dev, &base_v, &epoch);
     if (s != RPQ_OK) return s;
     uint8_t *base = static_cast<uint8_t *>(base_v);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1636,15 +2264,19 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     p.final_mask = a.final_mask;
     p.alpha = env_float("RPQ_PULL_ALPHA", g->pull_alpha);
     p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
+    p.solo_mass = g->solo_mass;
+    p.solo_items = g->solo_items;
+    // the scratch layout moves with the automaton's size: clear P / F first
+    p.clear_first = 1;
     p.groups = reinterpret_cast<const QGroup *>(base + x_tab + o_groups);
     p.units = reinterpret_cast<const QUnit *>(base + x_tab + o_units);
     p.t_unit = reinterpret_cast<const int32_t *>(base + x_tab + o_tu);
     p.t_state = reinterpret_cast<const int32_t *>(base + x_tab + o_ts);
     p.u_group = reinterpret_cast<const int32_t *>(base + x_tab + o_ug);
     p.P = reinterpret_cast<uint64_t *>(base + x_P);
+    p.VL = reinterpret_cast<int32_t *>(base + x_VL);
     for (int k = 0; k < 3; k++) {
         p.F[k] = reinterpret_cast<uint64_t *>(base + x_F[k]);
-        p.FL[k] = reinterpret_cast<int32_t *>(base + x_FL[k]);
         p.rows[k] = reinterpret_cast<Row *>(base + x_rows[k]);
         p.cmap[k] = reinterpret_cast<int32_t *>(base + x_cmap[k]);
     }
@@ -1656,11 +2288,11 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     p.out_list = out_vertices;
     p.capacity = out_vertices ? capacity : 0;
     p.out_bits = nullptr;
+    p.epoch = epoch;
     const size_t smem = shared_bytes(p.n_groups, p.n_units, p.n_targets, p.n_ugroups);
     int grid = 0;
     s = get_launch_shape(dev, smem, &grid);
     if (s != RPQ_OK) return s;
-    RPQ_CUDA_TRY(cudaMemsetAsync(&p.c->status, 0, sizeof(int32_t), st));
     void *args[] = {&p};
     RPQ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)rpq_query_kernel, dim3(grid),
                                              dim3(kThreads), args, smem, st));

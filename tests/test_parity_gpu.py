@@ -302,3 +302,46 @@ def test_autotune_keeps_answers():
     for i in range(8):
         exp = og.ssr(oracle_compile(texts[i % 4], 4), srcs[i])["answer"]
         assert R.rpq_query(gg, nfas[i], srcs[i]).tolist() == exp.tolist()
+
+
+SOLO = [(-1, 0), (2048, 256), (1 << 30, 1 << 30)]  # never, default, whenever no unit pulls
+SOLO_IDS = ["grid_only", "solo_default", "solo_max"]
+
+
+@pytest.mark.parametrize("solo", SOLO, ids=SOLO_IDS)
+@pytest.mark.parametrize("pull_mode", [(1e9, 0), (4.0, 256)], ids=["pull", "auto"], indirect=True)
+def test_solo_levels_and_workspace_reuse(solo, pull_mode, monkeypatch):
+    """Levels run on the whole grid or on one CTA (with the switches between
+    them), and every query leaves its workspace clean for the next: an
+    interleaved sequence of queries on one graph, each against the oracle,
+    then the first ones again."""
+    monkeypatch.setenv("RPQ_SOLO_MASS", str(solo[0]))
+    monkeypatch.setenv("RPQ_SOLO_ITEMS", str(solo[1]))
+    g = W.rmat_graph(14, 1 << 18, 4, seed=63)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    texts = ["0*", "1/(0|2)*", "(0|^1)*/2", "^0/1*", "3/3/3", "(0/1)*", "2"]
+    srcs = W.below(64, 1, 14, g.n).tolist()
+    jobs = [(texts[i % len(texts)], srcs[i]) for i in range(14)]
+    exp = [og.ssr(oracle_compile(t, 4), s) for t, s in jobs]
+    for (t, s), o in zip(jobs, exp):
+        nfa = R.rpq_nfa_compile(t, 4)
+        got, st = R.rpq_query(gg, nfa, s, with_stats=True)
+        assert got.tolist() == o["answer"].tolist(), (t, s)
+        # the counters depend on the automaton: compare with the oracle run
+        # on the library's own (minimised) automaton
+        e = nfa.export()
+        same = Nfa(e["n_states"], 4, list(zip(e["from"].tolist(), e["label"].tolist(),
+                                                e["to"].tolist())), e["starts"], e["finals"])
+        check_counters(st, og.ssr(same, s)["counters"])
+    for (t, s), o in zip(jobs[:5], exp[:5]):
+        assert gpu_regex(gg, t, 4, s).tolist() == o["answer"].tolist(), (t, s)
+    # bitset output and a level cap go through the grid-wide answer sweep
+    for (t, s) in jobs[:4]:
+        bits = np.zeros((g.n + 63) // 64, np.uint64)
+        R.rpq_query_bitset(gg, R.rpq_nfa_compile(t, 4), s, out=bits)
+        ids = np.nonzero(np.unpackbits(bits.view(np.uint8), bitorder="little"))[0]
+        assert ids.tolist() == og.ssr(oracle_compile(t, 4), s)["answer"].tolist()
+        k = 2
+        assert gpu_regex(gg, t, 4, s, k).tolist() == \
+            og.ssr(oracle_compile(t, 4), s, k)["answer"].tolist()
