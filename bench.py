@@ -167,7 +167,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -236,6 +236,19 @@ def workload_config(w, n_queries, extra=None):
 
 
 # ---------------------------------------------------------- CPU oracle ----
+
+def autotune(R, gg, g, name):
+    """The push/pull threshold picked by the library's autotuner on a sample
+    of queries drawn apart from the timed ones (other seed), before timing."""
+    from paper_2412_10287_gb300 import workloads as W
+
+    tpl = W.TEMPLATES_KB if name == "kb20m" else W.TEMPLATES_SMALL
+    sample = W.make_queries(g, tpl, 4, seed=99, zipf_s=1.1 if name == "kb20m" else 1.0)
+    alpha, mn = R.rpq_graph_autotune(gg, [R.rpq_nfa_compile(q.regex, g.n_labels) for q in sample],
+                                     [q.source for q in sample])
+    return {"pull_alpha": alpha, "pull_min": mn,
+            "sample": f"{len(sample)} queries of the same templates, seed 99"}
+
 
 def oracle_sample(w, seconds_budget, max_threads=None):
     """Times the CPU oracle (as it stands) on a stratified sample of the
@@ -564,6 +577,7 @@ def main():
                  args.workload)
     g = w.graph
     gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    tuned = autotune(R, gg, g, args.workload)
     nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
     srcs = [q.source for q in w.queries]
     nq = len(srcs)
@@ -651,7 +665,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(w, nq),
+            "config": workload_config(w, nq, {"autotuned": tuned}),
             "p50_ms": p50, "p99_ms": p99,
             "product_edges_per_s": ws * prod_edges / (total_s if ws == 1 else total_s),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -659,6 +673,7 @@ def main():
                          "kernel": "rpq_query_kernel",
                          "peak_kind": f"{peak_kind} copy bandwidth",
                          "algorithmic_bytes_per_launch": alg_bytes_per_launch,
+                         "achieved_push_bytes_only": push_bytes / len(recs) / avg_launch_s / 1e9,
                          "avg_launch_ms": avg_launch_s * 1000.0},
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

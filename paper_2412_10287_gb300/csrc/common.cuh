@@ -43,6 +43,10 @@ struct DevAdj {
     const int32_t *rows;   // hyper: sorted ids of the non-empty rows
     const int32_t *off;    // dense: [n+1]; hyper: [nrows+1]; relative to nbr
     const int32_t *nbr;    // neighbour ids, sorted within each row
+    // hyper: bucket b holds the ids [b << bbits, (b+1) << bbits); bkt[b] is
+    // the first row index with an id in it or after it (about 4 rows a bucket)
+    const int32_t *bkt;
+    int32_t bbits, pad;
 };
 
 // Row v of an adjacency as [b, e) into nbr.
@@ -51,14 +55,27 @@ __device__ __forceinline__ void adj_row(const DevAdj &A, int32_t v, int32_t &b, 
         b = __ldg(A.off + v);
         e = __ldg(A.off + v + 1);
     } else if (A.fmt == ADJ_HYPER) {
-        int32_t lo = 0, hi = A.nrows;  // first index with rows[idx] >= v
-        while (lo < hi) {
-            int32_t mid = (lo + hi) >> 1;
-            if (__ldg(A.rows + mid) < v) lo = mid + 1; else hi = mid;
+        // v's bucket, then v among the bucket's few row ids
+        const int32_t bi = v >> A.bbits;
+        int32_t lo = __ldg(A.bkt + bi), hi = __ldg(A.bkt + bi + 1);
+        int32_t at = -1;
+        if (hi - lo <= 8) {
+            int32_t x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) x[r] = lo + r < hi ? __ldg(A.rows + lo + r) : -1;
+#pragma unroll
+            for (int r = 0; r < 8; r++)
+                if (x[r] == v) at = lo + r;
+        } else {
+            while (lo < hi) {  // first index with rows[idx] >= v
+                const int32_t mid = (lo + hi) >> 1;
+                if (__ldg(A.rows + mid) < v) lo = mid + 1; else hi = mid;
+            }
+            if (lo < A.nrows && __ldg(A.rows + lo) == v) at = lo;
         }
-        if (lo < A.nrows && __ldg(A.rows + lo) == v) {
-            b = __ldg(A.off + lo);
-            e = __ldg(A.off + lo + 1);
+        if (at >= 0) {
+            b = __ldg(A.off + at);
+            e = __ldg(A.off + at + 1);
         } else {
             b = e = 0;
         }

@@ -251,6 +251,26 @@ __global__ void dense_offsets_kernel(const int32_t *maj, int64_t s, int64_t e, i
 }
 
 // hypersparse rows of one label segment
+// bkt[b] = first index of rows (sorted ids, nrows of them) with id >= b << bbits,
+// for b in [0, nb]; bkt[nb] = nrows.
+__global__ void bucket_index_kernel(const int32_t *rows, int32_t nrows, int32_t bbits, int64_t nb,
+                                    int32_t *bkt) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nb;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        if (b == nb) {
+            bkt[b] = nrows;
+            continue;
+        }
+        const int64_t v0 = b << bbits;
+        int32_t lo = 0, hi = nrows;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if ((int64_t)rows[mid] < v0) lo = mid + 1; else hi = mid;
+        }
+        bkt[b] = lo;
+    }
+}
+
 __global__ void hyper_rows_kernel(const int32_t *maj, const int32_t *rf, const int64_t *rscan,
                                   int64_t s, int64_t e, int32_t *rows, int32_t *off) {
     const int64_t cnt = e - s;
@@ -389,8 +409,8 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
         RPQ_CUDA_TRY(cudaStreamSynchronize(st));
     }
     // formats
-    int64_t dense_words = 0, hyper_rows_total = 0, hyper_off_total = 0;
-    std::vector<int32_t> fmt(L);
+    int64_t dense_words = 0, hyper_rows_total = 0, hyper_off_total = 0, bucket_total = 0;
+    std::vector<int32_t> fmt(L), bbits(L, 0);
     for (int32_t a = 0; a < L; a++) {
         const int64_t nnz = start[a + 1] - start[a];
         if (nnz >= (int64_t(1) << 31)) return fail(RPQ_ERR_INVALID, "label %d has >= 2^31 edges", a);
@@ -398,15 +418,24 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
         else if (rows[a] * 16 >= (int64_t)n || n <= 65536) fmt[a] = ADJ_DENSE;
         else fmt[a] = ADJ_HYPER;
         if (fmt[a] == ADJ_DENSE) dense_words += (int64_t)n + 1;
-        if (fmt[a] == ADJ_HYPER) { hyper_rows_total += rows[a]; hyper_off_total += rows[a] + 1; }
+        if (fmt[a] == ADJ_HYPER) {
+            hyper_rows_total += rows[a];
+            hyper_off_total += rows[a] + 1;
+            // largest bucket width with at most ~4 non-empty rows a bucket on average
+            while (bbits[a] < 30 && (int64_t(2) << bbits[a]) * rows[a] <= 4 * (int64_t)n)
+                bbits[a]++;
+            bucket_total += (((int64_t)n - 1) >> bbits[a]) + 2;
+        }
     }
-    std::unique_ptr<DevBuf> dense_p(new DevBuf()), hrows_p(new DevBuf()), hoff_p(new DevBuf());
-    DevBuf &dense_buf = *dense_p, &hrows_buf = *hrows_p, &hoff_buf = *hoff_p;
+    std::unique_ptr<DevBuf> dense_p(new DevBuf()), hrows_p(new DevBuf()), hoff_p(new DevBuf()),
+        bkt_p(new DevBuf());
+    DevBuf &dense_buf = *dense_p, &hrows_buf = *hrows_p, &hoff_buf = *hoff_p, &bkt_buf = *bkt_p;
     if (!dense_buf.alloc(sizeof(int32_t) * std::max<int64_t>(dense_words, 1)) ||
         !hrows_buf.alloc(sizeof(int32_t) * std::max<int64_t>(hyper_rows_total, 1)) ||
-        !hoff_buf.alloc(sizeof(int32_t) * std::max<int64_t>(hyper_off_total, 1)))
+        !hoff_buf.alloc(sizeof(int32_t) * std::max<int64_t>(hyper_off_total, 1)) ||
+        !bkt_buf.alloc(sizeof(int32_t) * std::max<int64_t>(bucket_total, 1)))
         return fail(RPQ_ERR_OOM, "graph offsets");
-    int64_t dpos = 0, hrpos = 0, hopos = 0;
+    int64_t dpos = 0, hrpos = 0, hopos = 0, bpos = 0;
     for (int32_t a = 0; a < L; a++) {
         DevAdj A{};
         A.fmt = fmt[a];
@@ -430,8 +459,15 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
             A.rows = rw;
             A.off = off;
             A.nrows = (int32_t)rows[a];
+            const int64_t nb = (((int64_t)n - 1) >> bbits[a]) + 1;
+            int32_t *bk = bkt_buf.as<int32_t>() + bpos;
+            bucket_index_kernel<<<grid_for(nb + 1), 256, 0, st>>>(rw, A.nrows, bbits[a], nb, bk);
+            RPQ_CUDA_TRY(cudaGetLastError());
+            A.bkt = bk;
+            A.bbits = bbits[a];
             hrpos += rows[a];
             hopos += rows[a] + 1;
+            bpos += nb + 1;
         }
         g->adj[dir0 + a] = A;
     }
@@ -439,6 +475,7 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
     g->owned.push_back(std::move(dense_p));
     g->owned.push_back(std::move(hrows_p));
     g->owned.push_back(std::move(hoff_p));
+    g->owned.push_back(std::move(bkt_p));
     if (!csc) {
         g->nnz.assign(L, 0);
         for (int32_t a = 0; a < L; a++) g->nnz[a] = start[a + 1] - start[a];

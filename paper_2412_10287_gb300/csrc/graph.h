@@ -38,7 +38,7 @@ struct rpq_graph {
     std::vector<std::unique_ptr<rpq::DevBuf>> owned;  // offsets / hypersparse rows
 
     // push/pull threshold used by single queries (set by rpq_graph_autotune)
-    float pull_alpha = 4.0f;
+    float pull_alpha = 2.0f;
     int32_t pull_min = 256;
     // a level runs on one CTA, with no grid barrier, while its push edge mass
     // and frontier items stay within these (solo_mass < 0: never)

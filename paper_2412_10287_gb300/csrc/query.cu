@@ -155,7 +155,8 @@ struct KParams {
     alignas(16) uint8_t tab[kInlineTables];
 };
 
-constexpr int kTraceFields = 8;  // t_plan, t_expand, t_barrier, pairs, push units, pull units, grid
+constexpr int kTraceFields = 8;  // t_plan, t_expand, t_barrier, pairs, push units, pull units,
+                                 // grid, push bytes of the level's rows
 constexpr int kTraceLevels = 4096;
 
 __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsigned long long v) {
@@ -459,6 +460,7 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
     }
     if (!total) return;
     const unsigned lane = lane_id();
+    const int g_first = gsf[q2], g_end = gsf[q2 + 1];
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&p.c->fl_count[L.slot][q2], (unsigned long long)total);
     base = __shfl_sync(kFull, base, 0);
@@ -475,7 +477,7 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
         run += __popc(m[r]);
     }
     unsigned long long acc_b = 0, acc_e = 0;
-    for (int g = gsf[q2]; g < gsf[q2 + 1]; g++) {
+    for (int g = g_first; g < g_end; g++) {
         const DevAdj A = p.adj[sh.gd[g]];
         int32_t rb[kB], re[kB];
 #pragma unroll
@@ -667,13 +669,19 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         const Row *R = p.rows[cs];
         const int32_t *CM = p.cmap[cs];
         const long long stride = (long long)ncta * kWarps;
-        for (long long c = (long long)cta + (long long)warp * ncta; c < nchunks; c += stride) {
-            const int ri = __ldcg(CM + c);
-            const int g = __ldcg(&R[ri].g);
+        long long c = (long long)cta + (long long)warp * ncta;
+        int ri_next = c < nchunks ? __ldcg(CM + c) : 0;
+        for (; c < nchunks; c += stride) {
+            // this chunk's row record and the next chunk's row index: one round trip
+            const int ri = ri_next;
+            const int2 gv = __ldcg(reinterpret_cast<const int2 *>(&R[ri].g));
+            const int2 be = __ldcg(reinterpret_cast<const int2 *>(&R[ri].b));
+            const long long c0r = __ldcg(&R[ri].chunk0);
+            ri_next = c + stride < nchunks ? __ldcg(CM + c + stride) : 0;
+            const int g = gv.x;
             const uint64_t tmv = sh.tpush[g];
             if (!tmv) continue;  // warp-uniform
-            const int32_t rb = __ldcg(&R[ri].b), re = __ldcg(&R[ri].e);
-            const long long c0r = __ldcg(&R[ri].chunk0);
+            const int32_t rb = be.x, re = be.y;
             const int32_t b = rb + (int32_t)((c - c0r) * kChunk);
             const int32_t e = min(re, b + kChunk);
             const int32_t *nbr = sh.gnbr[g];
@@ -1607,6 +1615,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             p.trace[(size_t)j * kTraceFields + 4] = (unsigned long long)p.n_units - npull;
             p.trace[(size_t)j * kTraceFields + 5] = npull;
             p.trace[(size_t)j * kTraceFields + 6] = grid ? 1 : 0;
+            p.trace[(size_t)j * kTraceFields + 7] = sh.lvl[0];
         }
         expand_phase(p, j, sh, s_gsf, &s_claim, s_acc, grid ? (int)blockIdx.x : 0,
                      grid ? (int)gridDim.x : 1, grid, grid && prev_grid);
@@ -1851,8 +1860,8 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
 
 // Appends one JSON line per query: the kernel's phase times and, per level,
 // block 0's timestamps (ns, relative to the kernel start) with the frontier
-// size, the number of push / pull units and whether the level ran on the
-// whole grid (1) or on CTA 0 alone (0).
+// size, the number of push / pull units, whether the level ran on the
+// whole grid (1) or on CTA 0 alone (0), and the push-model bytes of its rows.
 void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int levels,
                  cudaStream_t st) {
     std::vector<unsigned long long> h((size_t)kTraceFields * levels), gs(kTraceFields);
@@ -1873,8 +1882,8 @@ void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int le
     for (int j = 0; j < levels; j++) {
         const unsigned long long *r = &h[(size_t)j * kTraceFields];
         if (r[0] == 0) break;
-        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu, %llu]", j ? ", " : "", rel(r[0]),
-                rel(r[1]), rel(r[2]), r[3], r[4], r[5], r[6]);
+        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu, %llu, %llu]", j ? ", " : "",
+                rel(r[0]), rel(r[1]), rel(r[2]), r[3], r[4], r[5], r[6], r[7]);
     }
     fprintf(f, "]}\n");
     fclose(f);
