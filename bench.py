@@ -214,6 +214,30 @@ def workload(per_template, name="rmat20"):
     return W.config2(per_template=per_template)
 
 
+# query templates, seed and label skew of each single-query workload
+QUERY_SPECS = {"rmat20": ("TEMPLATES_SMALL", 1, 1.0), "kb20m": ("TEMPLATES_KB", 2, 1.1)}
+
+
+def rank_queries(g, name, per_template, rank):
+    """The queries rank `rank` runs (weak scaling: every rank its own units).
+    Rank 0 runs the workload's own queries; rank r > 0 an equally sized set
+    drawn the same way with its own seed."""
+    from paper_2412_10287_gb300 import workloads as W
+
+    tpl, seed, zipf = QUERY_SPECS[name]
+    return W.make_queries(g, getattr(W, tpl), per_template,
+                          seed=seed if rank == 0 else seed + 7919 * rank, zipf_s=zipf)
+
+
+def max_over_ranks(seconds, dist, device=None):
+    """The slowest rank's time (the job's time), through one all-reduce."""
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(w, n_queries, extra=None):
     if w.name == "kb20m":
         desc = ("kb20m: Chung-Lu power-law graph, 20,000,000 vertices, 200,000,000 edges "
@@ -573,8 +597,10 @@ def main():
     __graft_entry__.build()
     from paper_2412_10287_gb300 import rpq as R
 
-    w = workload(args.per_template if args.workload == "rmat20" else min(args.per_template, 25),
-                 args.workload)
+    per_template = args.per_template if args.workload == "rmat20" else min(args.per_template, 25)
+    w = workload(per_template, args.workload)
+    if rank > 0:
+        w.queries = rank_queries(w.graph, args.workload, per_template, rank)
     g = w.graph
     gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
     tuned = autotune(R, gg, g, args.workload)
@@ -619,9 +645,7 @@ def main():
     clocks = clk.summary()
     total_s = sum(step_ms) / 1000.0
     if ws > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+        total_s = max_over_ranks(total_s, torch.distributed, "cuda")
     value = ws * nq * args.steps / total_s
 
     lat = sorted(r[0] * 1000.0 for r in recs)
@@ -650,9 +674,7 @@ def main():
         e2e_steps.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_steps)
     if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, torch.distributed, "cuda")
     e2e_value = ws * nq * args.steps / e2e_s
 
     cpu = None
