@@ -52,7 +52,9 @@ constexpr int kR = 4;                 // edges per lane per round in the batched
 constexpr int kWarpRow = rpq_graph::kLongRow;  // rows with at least this many edges are chunked
 constexpr int kChunk = 32 * kR;       // edges per chunk: one warp round
 static_assert(kChunk == rpq_graph::kLongChunk, "chunk size must match the graph's row statistics");
-constexpr int kPullBatch = 8;         // in-neighbours a pull lane tests per round trip
+constexpr int kPullRows = 2;          // in-rows a pull thread tests together
+constexpr int kPullBatch = 4;         // in-neighbours per row a pull lane tests per round trip
+constexpr int kPullTile = kThreads * kPullRows;  // in-rows per pull tile claim
 constexpr int kGather = 1024;         // gather buffer entries per CTA
 constexpr int kMaxGroups = 512;
 constexpr int kMaxUnits = 512;
@@ -607,18 +609,35 @@ __device__ __forceinline__ void relax_batch(const KParams &p, const Shared &sh, 
 // ---------------------------------------------------------------- phases -
 // Tile claims of CTA `cta` of `ncta` working CTAs: the first tile of every
 // CTA is static, later ones come from a counter that therefore starts past
-// the static ones; a CTA working alone just steps.  CTA-uniform result.
-__device__ __forceinline__ long long claim_block(unsigned long long *ctr, long long *s_claim,
-                                                 int k, long long tile, int cta, int ncta) {
-    if (k == 0) return (long long)cta * tile;
-    if (ncta == 1) return (long long)k * tile;
-    if (threadIdx.x == 0)
-        *s_claim = (long long)ncta * tile + (long long)atomicAdd(ctr, (unsigned long long)tile);
-    __syncthreads();
-    const long long t = *s_claim;
-    __syncthreads();
-    return t;
-}
+// the static ones; a CTA working alone just steps.  Thread 0 asks for the
+// next tile as soon as the current one is known, so the counter's round
+// trip overlaps the tile's work.  CTA-uniform results.
+struct TileClaims {
+    unsigned long long *ctr;
+    long long tile;
+    int cta, ncta;
+    int k = 0;
+    long long next = 0;  // thread 0: the tile claimed ahead
+    __device__ TileClaims(unsigned long long *c, long long t, int a, int n)
+        : ctr(c), tile(t), cta(a), ncta(n) {}
+    __device__ __forceinline__ long long take(long long *s_claim, long long total) {
+        long long t;
+        if (k == 0) {
+            t = (long long)cta * tile;
+        } else if (ncta == 1) {
+            t = (long long)k * tile;
+        } else {
+            if (threadIdx.x == 0) *s_claim = next;
+            __syncthreads();
+            t = *s_claim;
+            __syncthreads();
+        }
+        k++;
+        if (ncta > 1 && threadIdx.x == 0 && t < total)
+            next = (long long)ncta * tile + (long long)atomicAdd(ctr, (unsigned long long)tile);
+        return t;
+    }
+};
 
 // Level j on CTA `cta` of `ncta` working CTAs (the whole grid, or CTA 0
 // alone for a small level).  Frontier bits (read only by pull) are kept for
@@ -705,8 +724,9 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     const long long total_items = sh.gpref[p.n_groups];
     const long long item_tile =
         min((long long)kThreads, max(8LL, ((total_items + ncta - 1) / ncta + 7) & ~7LL));
-    for (int k = 0; total_items > 0; k++) {
-        const long long t0 = claim_block(&p.c->claim_item[cs], s_claim, k, item_tile, cta, ncta);
+    TileClaims item_claims(&p.c->claim_item[cs], item_tile, cta, ncta);
+    while (total_items > 0) {
+        const long long t0 = item_claims.take(s_claim, total_items);
         if (t0 >= total_items) break;
         const long long i = t0 + threadIdx.x;
         int g = -1;
@@ -777,12 +797,13 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         }
     }
 
-    // (3) pull units: sweep the rows of the in-adjacency
+    // (3) pull units: sweep the rows of the in-adjacency, kPullRows rows per
+    //     thread with their round trips overlapped
     const long long total_rows = sh.upref[p.n_units];
-    for (int k = 0; total_rows > 0; k++) {
-        const long long t0 = claim_block(&p.c->claim_pull[cs], s_claim, k, kThreads, cta, ncta);
+    TileClaims pull_claims(&p.c->claim_pull[cs], kPullTile, cta, ncta);
+    while (total_rows > 0) {
+        const long long t0 = pull_claims.take(s_claim, total_rows);
         if (t0 >= total_rows) break;
-        const long long i = t0 + threadIdx.x;
         int u = 0;
         {
             int lo = 0, hi = p.n_units - 1;
@@ -795,58 +816,84 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         const DevAdj A = p.adj[sh.uin[u]];
         const int uq2 = sh.uq2[u];
         const uint64_t usm = sh.usmask[u];
-        const long long r = i - sh.upref[u];
-        int32_t w = 0, rb = 0, re = 0;
-        bool cand = false;
-        if (r < sh.urows[u]) {
-            if (A.fmt == ADJ_DENSE) {
-                w = (int32_t)r;
-                rb = __ldg(A.off + w);
-                re = __ldg(A.off + w + 1);
-            } else {
-                w = __ldg(A.rows + r);
-                rb = __ldg(A.off + r);
-                re = __ldg(A.off + r + 1);
+        int32_t w[kPullRows], rb[kPullRows], re[kPullRows];
+        bool cand[kPullRows], found[kPullRows], pending[kPullRows];
+#pragma unroll
+        for (int h = 0; h < kPullRows; h++) {
+            const long long r = t0 + h * kThreads + threadIdx.x - sh.upref[u];
+            w[h] = rb[h] = re[h] = 0;
+            cand[h] = found[h] = pending[h] = false;
+            if (r < sh.urows[u]) {
+                if (A.fmt == ADJ_DENSE) {
+                    w[h] = (int32_t)r;
+                    rb[h] = __ldg(A.off + w[h]);
+                    re[h] = __ldg(A.off + w[h] + 1);
+                } else {
+                    w[h] = __ldg(A.rows + r);
+                    rb[h] = __ldg(A.off + r);
+                    re[h] = __ldg(A.off + r + 1);
+                }
+                cand[h] = true;
             }
-            cand = (re > rb) &&
-                   !((__ldcg(p.P + (size_t)uq2 * p.W + ((uint32_t)w >> 6)) >> (w & 63)) & 1ull);
         }
-        bool found = false, pending = false;
-        if (cand) {
-            // up to kWarpRow in-neighbours, kPullBatch at a time: their ids,
-            // then their frontier bits, each batch in one round trip
-            const int32_t lim = min(re, rb + kWarpRow);
-            for (int32_t k0 = rb; k0 < lim && !found; k0 += kPullBatch) {
-                int32_t x[kPullBatch];
 #pragma unroll
-                for (int r = 0; r < kPullBatch; r++)
-                    x[r] = k0 + r < lim ? __ldg(A.nbr + k0 + r) : -1;
-                uint64_t sm = usm;
-                while (sm && !found) {
-                    const int q = __ffsll((long long)sm) - 1;
-                    sm &= sm - 1;
-                    const uint64_t *Fq = F + (size_t)q * p.W;
-                    uint64_t fw[kPullBatch];
+        for (int h = 0; h < kPullRows; h++)
+            cand[h] = cand[h] && re[h] > rb[h] &&
+                      !((__ldcg(p.P + (size_t)uq2 * p.W + ((uint32_t)w[h] >> 6)) >> (w[h] & 63)) &
+                        1ull);
+        // up to kWarpRow in-neighbours of each row, kPullBatch at a time:
+        // their ids, then their frontier bits, every row's batch together
+        for (int32_t step = 0; step < kWarpRow; step += kPullBatch) {
+            bool more = false;
 #pragma unroll
-                    for (int r = 0; r < kPullBatch; r++)
-                        fw[r] = x[r] >= 0 ? __ldcg(Fq + ((uint32_t)x[r] >> 6)) : 0ull;
+            for (int h = 0; h < kPullRows; h++)
+                more |= cand[h] && !found[h] && rb[h] + step < min(re[h], rb[h] + kWarpRow);
+            if (!more) break;
+            int32_t x[kPullRows][kPullBatch];
 #pragma unroll
-                    for (int r = 0; r < kPullBatch; r++)
-                        found |= x[r] >= 0 && ((fw[r] >> (x[r] & 63)) & 1ull);
+            for (int h = 0; h < kPullRows; h++) {
+                const int32_t lim = min(re[h], rb[h] + kWarpRow);
+                const bool live = cand[h] && !found[h];
+#pragma unroll
+                for (int r = 0; r < kPullBatch; r++) {
+                    const int32_t k = rb[h] + step + r;
+                    x[h][r] = live && k < lim ? __ldg(A.nbr + k) : -1;
                 }
             }
-            pending = !found && re - rb > kWarpRow;
+            uint64_t sm = usm;
+            while (sm) {
+                const int q = __ffsll((long long)sm) - 1;
+                sm &= sm - 1;
+                const uint64_t *Fq = F + (size_t)q * p.W;
+                uint64_t fw[kPullRows][kPullBatch];
+#pragma unroll
+                for (int h = 0; h < kPullRows; h++)
+#pragma unroll
+                    for (int r = 0; r < kPullBatch; r++)
+                        fw[h][r] = x[h][r] >= 0 ? __ldcg(Fq + ((uint32_t)x[h][r] >> 6)) : 0ull;
+#pragma unroll
+                for (int h = 0; h < kPullRows; h++)
+#pragma unroll
+                    for (int r = 0; r < kPullBatch; r++)
+                        found[h] |= x[h][r] >= 0 && ((fw[h][r] >> (x[h][r] & 63)) & 1ull);
+            }
         }
-        {
+#pragma unroll
+        for (int h = 0; h < kPullRows; h++)
+            pending[h] = cand[h] && !found[h] && re[h] - rb[h] > kWarpRow;
+        // rows of more than kWarpRow in-edges: the warp scans the rest of
+        // each, 32 in-neighbours a round, one row after the other
+#pragma unroll
+        for (int h = 0; h < kPullRows; h++) {
             unsigned m;
-            while ((m = __ballot_sync(kFull, pending)) != 0) {
+            while ((m = __ballot_sync(kFull, pending[h])) != 0) {
                 const int leader = __ffs(m) - 1;
-                const int32_t b = __shfl_sync(kFull, rb, leader) + kWarpRow;
-                const int32_t e = __shfl_sync(kFull, re, leader);
+                const int32_t b = __shfl_sync(kFull, rb[h], leader) + kWarpRow;
+                const int32_t e = __shfl_sync(kFull, re[h], leader);
                 bool hit = false;
                 for (int32_t base = b; base < e; base += 32) {
                     const int32_t k = base + (int32_t)lane;
-                    bool h = false;
+                    bool hk = false;
                     if (k < e) {
                         const int32_t x = __ldg(A.nbr + k);
                         uint64_t sm = usm;
@@ -855,30 +902,34 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
                             sm &= sm - 1;
                             if ((__ldcg(F + (size_t)q * p.W + ((uint32_t)x >> 6)) >> (x & 63)) &
                                 1ull) {
-                                h = true;
+                                hk = true;
                                 break;
                             }
                         }
                     }
-                    if (__ballot_sync(kFull, h)) {
+                    if (__ballot_sync(kFull, hk)) {
                         hit = true;
                         break;
                     }
                 }
                 if ((int)lane == leader) {
-                    pending = false;
-                    found = hit;
+                    pending[h] = false;
+                    found[h] = hit;
                 }
             }
         }
-        bool disc = false;
-        if (found) {
-            const uint64_t bit = 1ull << (w & 63);
-            const unsigned long long old = atomicOr(
-                (unsigned long long *)(p.P + (size_t)uq2 * p.W + ((uint32_t)w >> 6)), bit);
-            disc = !(old & bit);
+        bool disc[kPullRows];
+#pragma unroll
+        for (int h = 0; h < kPullRows; h++) {
+            disc[h] = false;
+            if (found[h]) {
+                const uint64_t bit = 1ull << (w[h] & 63);
+                const unsigned long long old = atomicOr(
+                    (unsigned long long *)(p.P + (size_t)uq2 * p.W + ((uint32_t)w[h] >> 6)), bit);
+                disc[h] = !(old & bit);
+            }
         }
-        warp_discover(p, sh, gsf, L, disc, uq2, w);
+        warp_discover_batch<kPullRows>(p, sh, gsf, L, disc, uq2, w);
     }
 
     // per-CTA sums of this level's discoveries
@@ -1017,7 +1068,7 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
         for (int u = 0; u < p.n_units; u++) {
             sh.upref[u] = ra;
             if (sh.upull[u]) {
-                ra += (sh.urows[u] + kThreads - 1) / kThreads * kThreads;
+                ra += (sh.urows[u] + kPullTile - 1) / kPullTile * kPullTile;
                 npull++;
             } else {
                 npush++;

@@ -347,16 +347,12 @@ def rpq_query(g: Graph, nfa: Nfa, source: int, max_levels: int = 0, out=None, st
     cnt = ctypes.c_int64()
     sp = ctypes.byref(st) if st is not None else None
     if out is None:
-        cap = 1 << 16
-        while True:
-            buf = np.empty(cap, np.int32)
-            s = _check(lib().rpq_query(g.h, nfa.h, int(source), int(max_levels), _ptr(buf), cap,
-                                       ctypes.byref(cnt), sp, _stream_handle(stream)),
-                       allow=(RPQ_ERR_CAPACITY,))
-            if s == RPQ_OK:
-                res = buf[: cnt.value].copy()
-                break
-            cap = int(cnt.value)
+        # an answer has at most n vertices: one call, never a second pass
+        buf = np.empty(g.n, np.int32)
+        _check(lib().rpq_query(g.h, nfa.h, int(source), int(max_levels), _ptr(buf), g.n,
+                               ctypes.byref(cnt), sp, _stream_handle(stream)))
+        c = int(cnt.value)
+        res = buf[:c].copy() if 4 * c < g.n else buf[:c]
     else:
         _check(lib().rpq_query(g.h, nfa.h, int(source), int(max_levels), _ptr(out), out.numel(),
                                ctypes.byref(cnt), sp, _stream_handle(stream)))
