@@ -184,6 +184,17 @@ rpq_status rpq_query(const rpq_graph *g, const rpq_nfa *nfa, int32_t source, int
                      int32_t *out_vertices, int64_t capacity, int64_t *out_count,
                      rpq_stats *stats, void *stream);
 
+/* The answer of the calling thread's most recent rpq_query whose output was
+ * not device memory -- also when out_vertices was NULL or too small, so that
+ * a caller can size its buffer from *out_count and copy the answer from here
+ * without a second traversal.  The paper has no counterpart (it is the
+ * second half of the two-call pattern).  *answer: *count vertex ids in
+ * ascending order, in library-owned pinned host memory that the kernel
+ * wrote directly; valid until this thread's next rpq_query call.
+ *   Errors: RPQ_ERR_INVALID (null argument, or the thread has no such
+ *   answer: its last rpq_query wrote device memory or failed). */
+rpq_status rpq_last_answer(const int32_t **answer, int64_t *count);
+
 /* Single-source query that allocates no device memory.  The paper has no
  * counterpart: this is for callers that must not allocate on the GPU --
  * code running where every byte of device memory is owned by another

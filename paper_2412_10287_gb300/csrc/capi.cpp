@@ -197,14 +197,21 @@ extern "C" rpq_status rpq_query(const rpq_graph *g, const rpq_nfa *nfa, int32_t 
     rpq_graph *gm = const_cast<rpq_graph *>(g);
     const bool dev = out_vertices && is_device_pointer(out_vertices);
     int64_t count = 0;
+    // a host answer (or none asked for) goes through the thread's pinned
+    // buffer, where rpq_last_answer finds it
     rpq_status s = run_query(gm, nfa->a, source, max_levels, dev ? out_vertices : nullptr, capacity,
-                             nullptr, dev ? nullptr : out_vertices, stats, &count, stream);
+                             nullptr, dev ? nullptr : out_vertices, stats, &count, stream, !dev);
     if (s != RPQ_OK) return s;
     *out_count = count;
     if (count > capacity)
         return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices, capacity %lld", (long long)count,
                     (long long)capacity);
     return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_last_answer(const int32_t **answer, int64_t *count) {
+    clear_error();
+    return last_host_answer(answer, count);
 }
 
 extern "C" rpq_status rpq_query_bitset(const rpq_graph *g, const rpq_nfa *nfa, int32_t source,

@@ -298,25 +298,31 @@ __global__ void rows_per_label_kernel(const int64_t *rscan, const int32_t *rf, c
 }
 
 // rows of at least `minlen` edges and their chunk count, for one adjacency
+// Per direction: rows of >= minlen edges, their chunks, and the non-empty
+// rows shorter than that.
 __global__ void long_rows_kernel(DevAdj A, int32_t minlen, int32_t chunk,
-                                 unsigned long long *out /* [2] */) {
+                                 unsigned long long *out /* [3] */) {
     const int64_t rows = A.fmt == ADJ_EMPTY ? 0 : A.nrows;
-    unsigned long long nr = 0, nc = 0;
+    unsigned long long nr = 0, nc = 0, ns = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t deg = A.off[r + 1] - A.off[r];
         if (deg >= minlen) {
             nr++;
             nc += (unsigned long long)((deg + chunk - 1) / chunk);
+        } else if (deg > 0) {
+            ns++;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         nr += __shfl_down_sync(kFull, nr, o);
         nc += __shfl_down_sync(kFull, nc, o);
+        ns += __shfl_down_sync(kFull, ns, o);
     }
-    if ((threadIdx.x & 31) == 0 && (nr || nc)) {
+    if ((threadIdx.x & 31) == 0 && (nr || nc || ns)) {
         atomicAdd(out, nr);
         atomicAdd(out + 1, nc);
+        atomicAdd(out + 2, ns);
     }
 }
 
@@ -584,28 +590,30 @@ extern "C" rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64
         rpq_status s = build_side(g.get(), side == 1, o[1], o[2], nb->as<int32_t>(), mu, st);
         if (s != RPQ_OK) return s;
     }
-    // long-row statistics per direction
+    // long- and short-row statistics per direction
     {
         DevBuf lr;
         const size_t nd = g->adj.size();
-        if (!lr.alloc(sizeof(unsigned long long) * 2 * nd)) return fail(RPQ_ERR_OOM, "row statistics");
-        RPQ_CUDA_TRY(cudaMemsetAsync(lr.p, 0, sizeof(unsigned long long) * 2 * nd, st));
+        if (!lr.alloc(sizeof(unsigned long long) * 3 * nd)) return fail(RPQ_ERR_OOM, "row statistics");
+        RPQ_CUDA_TRY(cudaMemsetAsync(lr.p, 0, sizeof(unsigned long long) * 3 * nd, st));
         for (size_t d = 0; d < nd; d++) {
             const DevAdj &A = g->adj[d];
             if (A.fmt == ADJ_EMPTY) continue;
             long_rows_kernel<<<grid_for(A.nrows), 256, 0, st>>>(
-                A, rpq_graph::kLongRow, rpq_graph::kLongChunk, lr.as<unsigned long long>() + 2 * d);
+                A, rpq_graph::kLongRow, rpq_graph::kLongChunk, lr.as<unsigned long long>() + 3 * d);
             RPQ_CUDA_TRY(cudaGetLastError());
         }
-        std::vector<unsigned long long> h(2 * nd);
-        RPQ_CUDA_TRY(cudaMemcpyAsync(h.data(), lr.p, sizeof(unsigned long long) * 2 * nd,
+        std::vector<unsigned long long> h(3 * nd);
+        RPQ_CUDA_TRY(cudaMemcpyAsync(h.data(), lr.p, sizeof(unsigned long long) * 3 * nd,
                                      cudaMemcpyDeviceToHost, st));
         RPQ_CUDA_TRY(cudaStreamSynchronize(st));
         g->long_rows.assign(nd, 0);
         g->long_chunks.assign(nd, 0);
+        g->short_rows.assign(nd, 0);
         for (size_t d = 0; d < nd; d++) {
-            g->long_rows[d] = (int64_t)h[2 * d];
-            g->long_chunks[d] = (int64_t)h[2 * d + 1];
+            g->long_rows[d] = (int64_t)h[3 * d];
+            g->long_chunks[d] = (int64_t)h[3 * d + 1];
+            g->short_rows[d] = (int64_t)h[3 * d + 2];
         }
     }
     if (!g->d_adj.alloc(sizeof(DevAdj) * g->adj.size())) return fail(RPQ_ERR_OOM, "adjacency table");

@@ -31,6 +31,8 @@ struct rpq_graph {
     // per direction d: rows with at least kLongRow edges, and the sum over
     // them of ceil(deg / kLongChunk) (sizes of the query kernel's row lists)
     std::vector<int64_t> long_rows, long_chunks;
+    // ... and its non-empty rows of fewer than kLongRow edges
+    std::vector<int64_t> short_rows;
     static constexpr int kLongRow = 32;
     static constexpr int kLongChunk = 128;
     rpq::DevBuf d_adj;         // device copy of adj

@@ -87,8 +87,7 @@ struct Row {
 // slot j % 3 holds level j.
 struct Counters {
     unsigned bar_count, bar_gen;
-    int32_t status, gate_cmd;
-    int32_t pub_level, pad0;
+    int32_t status, pub_level;
     unsigned long long gate;  // (launch epoch << 32) | releases of the gate so far
     unsigned long long beat;  // CTA 0's progress while it runs levels alone
     unsigned long long parked;  // CTAs that have parked (cumulative over the launch)
@@ -98,8 +97,21 @@ struct Counters {
     unsigned long long rows_packed[3];           // (rows << 40) | chunks
     unsigned long long lvl_bytes[3], lvl_edges[3];
     unsigned long long claim_chunk[3], claim_item[3], claim_pull[3];
-    long long levels, visited, expanded, product_edges, push_bytes;
-    long long push_units, pull_units, answer_count;
+    unsigned long long srows_count[3];  // short rows listed per level slot
+    long long answer_count;
+};
+
+// Where a level's counters live: device memory on grid levels or, while CTA
+// 0 runs levels alone, its shared memory (no round trips).  Slot j % 3
+// holds level j.
+struct Ctrs {
+    unsigned long long *fl;     // [3][kMaxStates] pairs per state
+    unsigned long long *rows;   // [3] long rows << 40 | chunks
+    unsigned long long *bytes;  // [3] push bytes of the level's rows
+    unsigned long long *edges;  // [3] product edges of the level's rows
+    unsigned long long *srows;  // [3] short rows listed
+    unsigned long long *mf;     // [3][mstride] edge mass per group
+    int32_t mstride, pad;
 };
 
 // Automaton tables of up to this many bytes travel inside the kernel's
@@ -109,11 +121,17 @@ constexpr int kInlineTables = 2048;
 // Query summary CTA 0 writes to host-mapped memory when the kernel ends, so
 // the host reads it (after synchronising the stream) without a device-to-host
 // copy.  A failed launch writes none: `epoch` then differs from the launch's.
+// the query's statistics, kept by CTA 0 in shared memory
+enum : int {
+    kStLevels, kStVisited, kStExpanded, kStProductEdges, kStPushBytes, kStPushUnits, kStPullUnits,
+    kStats
+};
+
 struct QueryResult {
     long long levels, visited, expanded, product_edges, push_bytes;
     long long push_units, pull_units, answer_count;
     uint32_t epoch;
-    int32_t pad;
+    int32_t small;  // 1: the answer went to out_list_small
 };
 
 struct KParams {
@@ -140,13 +158,15 @@ struct KParams {
     int32_t *VL;             // [S][n] visited vertices of each state, in discovery order
     Row *rows[3];            // long rows per level slot
     int32_t *cmap[3];        // chunk -> row index per level slot
-    long long row_cap, chunk_cap;
+    int4 *srl[3];            // short rows (group, begin, end, vertex) per level slot
+    long long row_cap, chunk_cap, srow_cap;
     unsigned long long *mf;  // [3][kMaxGroups]: frontier edge mass per group
     long long *fin_sums;     // [gridDim]
     Counters *c;
     // output
     int32_t *out_list;
     int64_t capacity;
+    int32_t *out_list_small;  // small answers (CTA 0 alone) go here instead, if set
     uint64_t *out_bits;  // bitset output (or nullptr)
     // optional per-level trace (block 0's view)
     unsigned long long *trace;
@@ -157,8 +177,9 @@ struct KParams {
     alignas(16) uint8_t tab[kInlineTables];
 };
 
-constexpr int kTraceFields = 8;  // t_plan, t_expand, t_barrier, pairs, push units, pull units,
-                                 // grid, push bytes of the level's rows
+constexpr int kTraceFields = 12;  // t_plan, t_expand, t_barrier, pairs, push units, pull units,
+                                  // grid, push bytes of the level's rows, block 0's chunks done,
+                                  // its short rows done, ~(first CTA done), last CTA done
 constexpr int kTraceLevels = 4096;
 
 __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsigned long long v) {
@@ -206,7 +227,9 @@ __device__ __forceinline__ bool grid_barrier(Counters *c) {
 // per-level control work never waits on global memory.
 struct Shared {
     uint64_t *tpush;    // push-mode targets of each group (decided per level)
-    long long *gpref;   // prefix of frontier items over push groups (n_groups + 1)
+    long long *nsrow;   // [2]: [0] short rows listed for the current level
+    long long *dpref;   // [n_groups + 1] prefix of frontier items over dense push groups
+    uint8_t *gdense;    // [n_groups] the group's adjacency has dense offsets
     const int32_t **gnbr;
     int32_t *gq, *gd, *gtpop;
     int32_t *gt_first, *gt_count;
@@ -226,13 +249,16 @@ struct Shared {
     int32_t *gbuf_k;
     int16_t *gbuf_g;
     unsigned long long *lvl;      // [2] level's push bytes / product edges (CTA 0's statistics)
+    long long *stats;             // [kStats] the query's statistics (CTA 0, thread 0)
+    unsigned long long *sctr;     // CTA 0's level counters in shared memory (Ctrs layout)
+    Ctrs *cv;                     // [2] counter views: device memory, shared memory
     int32_t *flags;               // [2] test P before the atomicOr (big levels); spare
 };
 
 template <class F>
 __host__ __device__ size_t shared_layout(int ng, int nu, int nt, int nug, F take) {
     take(0, sizeof(uint64_t) * ng);
-    take(1, sizeof(long long) * (ng + 1));
+    take(1, sizeof(long long) * 2);
     take(2, sizeof(void *) * ng);
     take(3, sizeof(int32_t) * ng);
     take(4, sizeof(int32_t) * ng);
@@ -261,7 +287,12 @@ __host__ __device__ size_t shared_layout(int ng, int nu, int nt, int nug, F take
     take(27, sizeof(long long) * kMaxStates);
     take(28, sizeof(long long) * kMaxStates);
     take(29, sizeof(unsigned long long) * 2);
-    return take(30, sizeof(int32_t) * 2);
+    take(30, sizeof(int32_t) * 2);
+    take(31, sizeof(long long) * kStats);
+    take(32, sizeof(unsigned long long) * (3 * kMaxStates + 12 + 3 * (size_t)ng));
+    take(33, sizeof(Ctrs) * 2);
+    take(34, sizeof(long long) * (ng + 1));
+    return take(35, ng);
 }
 
 __host__ __device__ size_t shared_bytes(int ng, int nu, int nt, int nug) {
@@ -275,7 +306,7 @@ __host__ __device__ size_t shared_bytes(int ng, int nu, int nt, int nug) {
 
 __device__ Shared carve(const KParams &p, uint8_t *base) {
     Shared s;
-    uint8_t *ptr[31];
+    uint8_t *ptr[36];
     size_t off = 0;
     shared_layout(p.n_groups, p.n_units, p.n_targets, p.n_ugroups, [&](int i, size_t bytes) {
         off = (off + 15) & ~size_t(15);
@@ -284,7 +315,7 @@ __device__ Shared carve(const KParams &p, uint8_t *base) {
         return off;
     });
     s.tpush = (uint64_t *)ptr[0];
-    s.gpref = (long long *)ptr[1];
+    s.nsrow = (long long *)ptr[1];
     s.gnbr = (const int32_t **)ptr[2];
     s.gq = (int32_t *)ptr[3];
     s.gd = (int32_t *)ptr[4];
@@ -314,6 +345,11 @@ __device__ Shared carve(const KParams &p, uint8_t *base) {
     s.vnext = (long long *)ptr[28];
     s.lvl = (unsigned long long *)ptr[29];
     s.flags = (int32_t *)ptr[30];
+    s.stats = (long long *)ptr[31];
+    s.sctr = (unsigned long long *)ptr[32];
+    s.cv = (Ctrs *)ptr[33];
+    s.dpref = (long long *)ptr[34];
+    s.gdense = (uint8_t *)ptr[35];
     return s;
 }
 
@@ -334,6 +370,7 @@ __device__ void load_tables(const KParams &p, const Shared &sh) {
         sh.gq[g] = G.q;
         sh.gd[g] = G.d;
         sh.gnbr[g] = p.adj[G.d].nbr;
+        sh.gdense[g] = p.adj[G.d].fmt == ADJ_DENSE ? 1 : 0;
         sh.gtpop[g] = __popcll(G.tmask);
         sh.gt_first[g] = G.t_first;
         sh.gt_count[g] = G.t_count;
@@ -367,18 +404,27 @@ __device__ void load_tables(const KParams &p, const Shared &sh) {
         sh.lvl[threadIdx.x] = 0;
         sh.flags[threadIdx.x] = 0;
     }
+    if (threadIdx.x < kStats) sh.stats[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < 3 * kMaxStates + 12 + 3 * p.n_groups; i += kThreads) sh.sctr[i] = 0;
+    if (threadIdx.x == 0) {
+        sh.cv[0] = Ctrs{&p.c->fl_count[0][0], p.c->rows_packed, p.c->lvl_bytes, p.c->lvl_edges,
+                        p.c->srows_count, p.mf, kMaxGroups, 0};
+        unsigned long long *b = sh.sctr + 3 * kMaxStates;
+        sh.cv[1] = Ctrs{sh.sctr, b, b + 3, b + 6, b + 9, b + 12, p.n_groups, 0};
+    }
     __syncthreads();
 }
 
 // ------------------------------------------------------------ discovery --
 struct LevelCtx {
     int slot;                     // slot of the level being discovered
+    const Ctrs *C;                // where its counters go
     int32_t *VL;
     const long long *vnext;       // first list entry of the level being discovered
     uint64_t *F;                  // frontier bits of that level, or null (not kept)
-    Row *rows;
-    int32_t *cmap;
     unsigned long long *s_acc;    // [2] per-CTA push bytes / product edges
+    // its long-row list, chunk map and short-row list are p.rows / p.cmap /
+    // p.srl[slot] (read from the parameters when used, not held in registers)
 };
 
 // Lanes with `found` have discovered the new pair (q2, w) of the next level.
@@ -393,7 +439,7 @@ __device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t 
     const int leader = __ffs(m) - 1;
     unsigned long long base = 0;
     if ((int)lane == leader)
-        base = atomicAdd(&p.c->fl_count[L.slot][q2], (unsigned long long)__popc(m));
+        base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)__popc(m));
     base = __shfl_sync(kFull, base, leader);
     if (found) {
         L.VL[(size_t)q2 * p.n + L.vnext[q2] + base + __popc(m & lanemask_lt())] = w;
@@ -411,6 +457,22 @@ __device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t 
             acc_b += 8ull + 4ull * (unsigned long long)deg;
             acc_e += (unsigned long long)deg * (unsigned long long)sh.gtpop[g];
         }
+        // short rows of a hypersparse adjacency: warp-aggregated append to the
+        // level's short-row list (dense ones are found again from the
+        // frontier list and the offsets, one round trip)
+        const bool sht = found && deg > 0 && deg < kWarpRow && !sh.gdense[g];
+        const unsigned msh = __ballot_sync(kFull, sht);
+        if (msh) {
+            const int ls = __ffs(msh) - 1;
+            unsigned long long sb = 0;
+            if ((int)lane == ls) sb = atomicAdd(&L.C->srows[L.slot], (unsigned long long)__popc(msh));
+            sb = __shfl_sync(kFull, sb, ls);
+            if (sht) {
+                const long long at = (long long)sb + __popc(msh & lanemask_lt());
+                if (at < p.srow_cap) p.srl[L.slot][at] = make_int4(g, rb, re, w);
+                else atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
+            }
+        }
         // long rows: warp-aggregated append to the chunk list
         const bool lng = found && deg >= kWarpRow;
         const unsigned ml = __ballot_sync(kFull, lng);
@@ -426,15 +488,15 @@ __device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t 
         const int ld = __ffs(ml) - 1;
         unsigned long long old = 0;
         if ((int)lane == ld)
-            old = atomicAdd(&p.c->rows_packed[L.slot],
+            old = atomicAdd(&L.C->rows[L.slot],
                             ((unsigned long long)__popc(ml) << 40) | (unsigned long long)tot);
         old = __shfl_sync(kFull, old, ld);
         if (lng) {
             const long long ri = (long long)(old >> 40) + __popc(ml & lanemask_lt());
             const long long cb = (long long)(old & ((1ull << 40) - 1)) + (incl - nch);
             if (ri < p.row_cap && cb + nch <= p.chunk_cap) {
-                L.rows[ri] = Row{g, w, rb, re, cb};
-                for (int k = 0; k < nch; k++) L.cmap[cb + k] = (int32_t)ri;
+                p.rows[L.slot][ri] = Row{g, w, rb, re, cb};
+                for (int k = 0; k < nch; k++) p.cmap[L.slot][cb + k] = (int32_t)ri;
             } else {
                 atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
             }
@@ -464,7 +526,7 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
     const unsigned lane = lane_id();
     const int g_first = gsf[q2], g_end = gsf[q2 + 1];
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.c->fl_count[L.slot][q2], (unsigned long long)total);
+    if (lane == 0) base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)total);
     base = __shfl_sync(kFull, base, 0);
     int32_t *lst = L.VL + (size_t)q2 * p.n + L.vnext[q2];
     uint64_t *Fq = L.F ? L.F + (size_t)q2 * p.W : nullptr;
@@ -488,7 +550,7 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
             if (found[r]) adj_row(A, w[r], rb[r], re[r]);
         }
         int nch[kB];
-        int my_rows = 0, my_chunks = 0;
+        int my_rows = 0, my_chunks = 0, my_short = 0;
         unsigned long long mass = 0;
 #pragma unroll
         for (int r = 0; r < kB; r++) {
@@ -501,34 +563,53 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
             nch[r] = (found[r] && deg >= kWarpRow) ? (deg + kChunk - 1) / kChunk : 0;
             my_rows += nch[r] ? 1 : 0;
             my_chunks += nch[r];
+            my_short += (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) ? 1 : 0;
         }
         if (mass) atomicAdd(&sh.s_mf[g], mass);
-        // warp prefix of (rows, chunks)
-        int ir = my_rows, ic = my_chunks;
+        // warp prefix of (short rows | long rows << 16, chunks); one
+        // reservation in each list, both in flight together
+        int ipk = my_short | (my_rows << 16), ic = my_chunks;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int yr = __shfl_up_sync(kFull, ir, o);
+            const int yp = __shfl_up_sync(kFull, ipk, o);
             const int yc = __shfl_up_sync(kFull, ic, o);
             if ((int)lane >= o) {
-                ir += yr;
+                ipk += yp;
                 ic += yc;
             }
         }
-        const int tr = __shfl_sync(kFull, ir, 31), tc = __shfl_sync(kFull, ic, 31);
-        if (!tr) continue;  // warp-uniform
-        unsigned long long old = 0;
-        if (lane == 0)
-            old = atomicAdd(&p.c->rows_packed[L.slot],
+        const int tpk = __shfl_sync(kFull, ipk, 31), tc = __shfl_sync(kFull, ic, 31);
+        const int ts = tpk & 0xffff, tr = tpk >> 16;
+        if (!ts && !tr) continue;  // warp-uniform
+        unsigned long long sb = 0, old = 0;
+        if (lane == 31 && ts) sb = atomicAdd(&L.C->srows[L.slot], (unsigned long long)ts);
+        if (lane == 0 && tr)
+            old = atomicAdd(&L.C->rows[L.slot],
                             ((unsigned long long)tr << 40) | (unsigned long long)tc);
+        sb = __shfl_sync(kFull, sb, 31);
         old = __shfl_sync(kFull, old, 0);
+        if (ts) {
+            long long at = (long long)sb + ((ipk & 0xffff) - my_short);
+#pragma unroll
+            for (int r = 0; r < kB; r++) {
+                const int32_t deg = re[r] - rb[r];
+                if (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) {
+                    if (at < p.srow_cap) p.srl[L.slot][at] = make_int4(g, rb[r], re[r], w[r]);
+                    else atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
+                    at++;
+                }
+            }
+        }
+        if (!tr) continue;  // warp-uniform
+        const int ir = ipk >> 16;
         long long ri = (long long)(old >> 40) + (ir - my_rows);
         long long cb = (long long)(old & ((1ull << 40) - 1)) + (ic - my_chunks);
 #pragma unroll
         for (int r = 0; r < kB; r++) {
             if (!nch[r]) continue;
             if (ri < p.row_cap && cb + nch[r] <= p.chunk_cap) {
-                L.rows[ri] = Row{g, w[r], rb[r], re[r], cb};
-                for (int k = 0; k < nch[r]; k++) L.cmap[cb + k] = (int32_t)ri;
+                p.rows[L.slot][ri] = Row{g, w[r], rb[r], re[r], cb};
+                for (int k = 0; k < nch[r]; k++) p.cmap[L.slot][cb + k] = (int32_t)ri;
             } else {
                 atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
             }
@@ -645,10 +726,14 @@ struct TileClaims {
 // bits exist and are cleared here.
 __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const int32_t *gsf,
                              long long *s_claim, unsigned long long *s_acc, int cta, int ncta,
-                             bool on_grid, bool clear_prev) {
+                             bool on_grid, bool clear_prev, bool cur_smem) {
     const int cs = j % 3, ns = (j + 1) % 3, os = (j + 2) % 3;
     const uint64_t *F = p.F[cs];
-    LevelCtx L{ns, p.VL, sh.vnext, on_grid ? p.F[ns] : nullptr, p.rows[ns], p.cmap[ns], s_acc};
+    // level j's counters are where the level before left them; level j+1's
+    // go to device memory on a grid level, to CTA 0's shared memory otherwise
+    const Ctrs &Cc = sh.cv[cur_smem ? 1 : 0];
+    const Ctrs &Cn = sh.cv[on_grid ? 0 : 1];
+    LevelCtx L{ns, &Cn, p.VL, sh.vnext, on_grid ? p.F[ns] : nullptr, s_acc};
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
@@ -666,12 +751,14 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         }
     }
     if (cta == 0) {
-        for (int i = threadIdx.x; i < p.S; i += kThreads) p.c->fl_count[os][i] = 0;
-        for (int i = threadIdx.x; i < p.n_groups; i += kThreads) p.mf[os * kMaxGroups + i] = 0;
+        // slot os serves level j+2, which may run in either mode: clear both
+        for (int k = 0; k < 2; k++) {
+            const Ctrs &C = sh.cv[k];
+            for (int i = threadIdx.x; i < p.S; i += kThreads) C.fl[os * kMaxStates + i] = 0;
+            for (int i = threadIdx.x; i < p.n_groups; i += kThreads) C.mf[os * C.mstride + i] = 0;
+            if (threadIdx.x == 0) C.rows[os] = C.bytes[os] = C.edges[os] = C.srows[os] = 0;
+        }
         if (threadIdx.x == 0) {
-            p.c->rows_packed[os] = 0;
-            p.c->lvl_bytes[os] = 0;
-            p.c->lvl_edges[os] = 0;
             p.c->claim_chunk[os] = 0;
             p.c->claim_item[os] = 0;
             p.c->claim_pull[os] = 0;
@@ -683,7 +770,7 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     //     (c / grid) % kWarps of it, so consecutive chunks (one long row)
     //     spread over all SMs; static, no claims
     {
-        const unsigned long long packed = *(volatile unsigned long long *)&p.c->rows_packed[cs];
+        const unsigned long long packed = *(volatile unsigned long long *)&Cc.rows[cs];
         const long long nchunks = (long long)(packed & ((1ull << 40) - 1));
         const Row *R = p.rows[cs];
         const int32_t *CM = p.cmap[cs];
@@ -718,10 +805,15 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         }
     }
 
-    // (2) short rows of push groups: CTA tiles of frontier items, scan-based
-    //     gather; a small frontier is spread over every CTA (tiles of 8 to
-    //     kThreads items)
-    const long long total_items = sh.gpref[p.n_groups];
+    trace_put(p, j, 8, global_timer_ns());
+    // (2) short rows of push groups: first the level's short-row list
+    //     (hypersparse groups: only non-empty rows, ranges known), then the
+    //     frontier items of dense groups (row found by its offsets); CTA
+    //     tiles of them, scan-based gather; a small level is spread over
+    //     every CTA (tiles of 8 to kThreads items)
+    const long long n_listed = sh.nsrow[0];
+    const long long total_items = n_listed + sh.dpref[p.n_groups];
+    const int4 *SRL = p.srl[cs];
     const long long item_tile =
         min((long long)kThreads, max(8LL, ((total_items + ncta - 1) / ncta + 7) & ~7LL));
     TileClaims item_claims(&p.c->claim_item[cs], item_tile, cta, ncta);
@@ -731,16 +823,26 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         const long long i = t0 + threadIdx.x;
         int g = -1;
         int32_t rb = 0, re = 0;
-        if (threadIdx.x < item_tile && i < total_items) {
-            int lo = 0, hi = p.n_groups - 1;  // last group with gpref <= i
+        if (threadIdx.x < item_tile && i < n_listed) {
+            const int4 e = __ldcg(SRL + i);
+            g = e.x;
+            if (sh.tpush[g]) {  // rows of groups that pull this level are skipped
+                rb = e.y;
+                re = e.z;
+            }
+        } else if (threadIdx.x < item_tile && i < total_items) {
+            const long long k = i - n_listed;
+            int lo = 0, hi = p.n_groups - 1;  // last group with dpref <= k
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (sh.gpref[mid] <= i) lo = mid; else hi = mid - 1;
+                if (sh.dpref[mid] <= k) lo = mid; else hi = mid - 1;
             }
             g = lo;
             const int q = sh.gq[g];
-            const int32_t v = __ldcg(p.VL + (size_t)q * p.n + sh.vstart[q] + (i - sh.gpref[g]));
-            adj_row(p.adj[sh.gd[g]], v, rb, re);
+            const int32_t v = __ldcg(p.VL + (size_t)q * p.n + sh.vstart[q] + (k - sh.dpref[g]));
+            const int32_t *off = p.adj[sh.gd[g]].off;
+            rb = __ldg(off + v);
+            re = __ldg(off + v + 1);
             if (re - rb >= kWarpRow) re = rb;  // expanded through the chunk list
         }
         const int32_t deg = re - rb;
@@ -797,6 +899,7 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
         }
     }
 
+    trace_put(p, j, 9, global_timer_ns());
     // (3) pull units: sweep the rows of the in-adjacency, kPullRows rows per
     //     thread with their round trips overlapped
     const long long total_rows = sh.upref[p.n_units];
@@ -937,13 +1040,18 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
         const unsigned long long v = sh.s_mf[g];
         if (v) {
-            atomicAdd(&p.mf[ns * kMaxGroups + g], v);
+            atomicAdd(&Cn.mf[ns * Cn.mstride + g], v);
             sh.s_mf[g] = 0;
         }
     }
     if (threadIdx.x == 0) {
-        if (s_acc[0]) atomicAdd(&p.c->lvl_bytes[ns], s_acc[0]);
-        if (s_acc[1]) atomicAdd(&p.c->lvl_edges[ns], s_acc[1]);
+        if (s_acc[0]) atomicAdd(&Cn.bytes[ns], s_acc[0]);
+        if (s_acc[1]) atomicAdd(&Cn.edges[ns], s_acc[1]);
+        if (p.trace && j < p.trace_cap) {  // spread of the CTAs' finishing times
+            const unsigned long long t = global_timer_ns();
+            atomicMax(&p.trace[(size_t)j * kTraceFields + 10], ~t);
+            atomicMax(&p.trace[(size_t)j * kTraceFields + 11], t);
+        }
     }
 }
 
@@ -952,18 +1060,22 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
 // current level becomes the previous one, and level j's frontier of state q
 // is the list range VL[q][vstart[q], vstart[q] + fl[q]).  All loads are
 // issued before the first use (one memory round trip).
-__device__ __forceinline__ void level_advance(const KParams &p, int j, const Shared &sh, bool account) {
+__device__ __forceinline__ void level_advance(const KParams &p, int j, const Shared &sh, bool account,
+                                              bool in_smem) {
     static_assert(kMaxGroups <= 2 * kThreads && kMaxStates <= kThreads, "one pass of loads");
     const int cs = j % 3;
     const int t = threadIdx.x, g1 = t + kThreads;
-    const unsigned long long fv =
-        t < p.S ? *(volatile unsigned long long *)&p.c->fl_count[cs][t] : 0ull;
-    const unsigned long long m0 = t < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + t) : 0ull;
-    const unsigned long long m1 = g1 < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + g1) : 0ull;
+    const Ctrs &C = sh.cv[in_smem ? 1 : 0];
+    const volatile unsigned long long *fl = C.fl + cs * kMaxStates;
+    const volatile unsigned long long *mf = C.mf + cs * C.mstride;
+    const unsigned long long fv = t < p.S ? fl[t] : 0ull;
+    const unsigned long long m0 = t < p.n_groups ? mf[t] : 0ull;
+    const unsigned long long m1 = g1 < p.n_groups ? mf[g1] : 0ull;
     unsigned long long lb = 0, le = 0;
+    const unsigned long long nsr = t == 0 ? *(volatile unsigned long long *)&C.srows[cs] : 0ull;
     if (account && t == 0) {
-        lb = *(volatile unsigned long long *)&p.c->lvl_bytes[cs];
-        le = *(volatile unsigned long long *)&p.c->lvl_edges[cs];
+        lb = *(volatile unsigned long long *)&C.bytes[cs];
+        le = *(volatile unsigned long long *)&C.edges[cs];
     }
     __syncthreads();
     if (t < kMaxStates) {
@@ -978,6 +1090,7 @@ __device__ __forceinline__ void level_advance(const KParams &p, int j, const Sha
     if (t == 0) {
         sh.lvl[0] = lb;
         sh.lvl[1] = le;
+        sh.nsrow[0] = (long long)nsr;
     }
     __syncthreads();
 }
@@ -994,7 +1107,10 @@ __device__ __forceinline__ void level_join(const KParams &p, int j, const Shared
     const long long vs = in ? __ldcg(&p.c->pub_vstart[t]) : 0;
     const unsigned long long m0 = t < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + t) : 0ull;
     const unsigned long long m1 = g1 < p.n_groups ? __ldcg(p.mf + cs * kMaxGroups + g1) : 0ull;
+    const unsigned long long nsr =
+        t == 0 ? *(volatile unsigned long long *)&p.c->srows_count[cs] : 0ull;
     __syncthreads();
+    if (t == 0) sh.nsrow[0] = (long long)nsr;
     if (t < kMaxStates) {
         sh.fl_prev[t] = (unsigned long long)fp;
         sh.vprev[t] = vp;
@@ -1022,12 +1138,12 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
     for (int q = 0; q < p.S; q++) total += (long long)sh.fl[q];
     const bool expand = total > 0 && (p.max_levels == 0 || j < p.max_levels);
     if (account && threadIdx.x == 0) {
-        p.c->visited += total;
-        if (total > 0 && j > 0) p.c->levels = j;
+        sh.stats[kStVisited] += total;
+        if (total > 0 && j > 0) sh.stats[kStLevels] = j;
         if (expand) {
-            p.c->expanded += total;
-            p.c->push_bytes += (long long)sh.lvl[0];
-            p.c->product_edges += (long long)sh.lvl[1];
+            sh.stats[kStExpanded] += total;
+            sh.stats[kStPushBytes] += (long long)sh.lvl[0];
+            sh.stats[kStProductEdges] += (long long)sh.lvl[1];
         }
     }
     if (!expand) return kPlanStop;
@@ -1054,16 +1170,17 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long acc = 0;
+        long long acc = 0;  // frontier items of dense push groups
         unsigned long long mass = 0;
         for (int g = 0; g < p.n_groups; g++) {
-            sh.gpref[g] = acc;
+            sh.dpref[g] = acc;
             if (sh.tpush[g]) {
-                acc += (long long)sh.fl[sh.gq[g]];
                 mass += sh.mfv[g];
+                if (sh.gdense[g]) acc += (long long)sh.fl[sh.gq[g]];
             }
         }
-        sh.gpref[p.n_groups] = acc;
+        sh.dpref[p.n_groups] = acc;
+        acc += sh.nsrow[0];  // plus the listed short rows: the items to gather
         long long ra = 0, npush = 0, npull = 0;
         for (int u = 0; u < p.n_units; u++) {
             sh.upref[u] = ra;
@@ -1076,8 +1193,8 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
         }
         sh.upref[p.n_units] = ra;
         if (account) {
-            p.c->push_units += npush;
-            p.c->pull_units += npull;
+            sh.stats[kStPushUnits] += npush;
+            sh.stats[kStPullUnits] += npull;
         }
         const bool solo = p.solo_mass >= 0 && npull == 0 &&
                           mass <= (unsigned long long)p.solo_mass && acc <= p.solo_items;
@@ -1092,9 +1209,10 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
 
 // ---------------------------------------------------------------- gate ---
 // While CTA 0 runs levels alone the other CTAs wait at the gate: a word
-// holding (launch epoch << 32) | releases so far.  Every CTA counts the
-// releases it has seen, so a CTA that arrives late still finds its release;
-// the epoch tells this launch's releases from a previous launch's.
+// holding (launch epoch << 32) | (command << 24) | releases so far.  Every
+// CTA counts the releases it has seen, so a CTA that arrives late still
+// finds its release; the epoch tells this launch's releases from a previous
+// launch's.
 constexpr int kGateLevel = 1;   // join the published level
 constexpr int kGateFinal = 2;   // join the grid-wide answer sweep after the published level
 constexpr int kGateDone = 3;    // the query is finished: exit
@@ -1113,9 +1231,9 @@ __device__ __forceinline__ int gate_wait(const KParams &p, unsigned &seen) {
         int cmd = kGateError;
         for (unsigned it = 1;; it++) {
             const unsigned long long gv = *gp;
-            if ((uint32_t)(gv >> 32) == p.epoch && (uint32_t)gv > seen) {
-                __threadfence();
-                cmd = *(volatile int32_t *)&p.c->gate_cmd;
+            if ((uint32_t)(gv >> 32) == p.epoch && ((uint32_t)gv & 0xffffffu) > seen) {
+                cmd = (int)((gv >> 24) & 0xffu);
+                if (cmd != kGateDone) __threadfence();  // before reading what CTA 0 published
                 break;
             }
             if ((it & 31u) == 0) {
@@ -1145,22 +1263,22 @@ __device__ __forceinline__ int gate_wait(const KParams &p, unsigned &seen) {
 // gate with `cmd`.
 __device__ __forceinline__ void gate_release(const KParams &p, const Shared &sh, unsigned &seen, int cmd,
                                              int j) {
-    if (cmd != kGateDone) {
-        for (int q = threadIdx.x; q < p.S; q += kThreads) {
-            p.c->pub_vstart[q] = sh.vstart[q];
-            p.c->pub_vprev[q] = sh.vprev[q];
-            p.c->pub_flprev[q] = (long long)sh.fl_prev[q];
-        }
+    const unsigned long long word = ((unsigned long long)p.epoch << 32) |
+                                    ((unsigned long long)cmd << 24) | (unsigned long long)(seen + 1);
+    seen++;
+    if (cmd == kGateDone) {  // nothing to publish: the parked CTAs just exit
+        if (threadIdx.x == 0) *(volatile unsigned long long *)&p.c->gate = word;
+        return;
     }
+    for (int q = threadIdx.x; q < p.S; q += kThreads) {
+        p.c->pub_vstart[q] = sh.vstart[q];
+        p.c->pub_vprev[q] = sh.vprev[q];
+        p.c->pub_flprev[q] = (long long)sh.fl_prev[q];
+    }
+    if (threadIdx.x == 0) *(volatile int32_t *)&p.c->pub_level = j;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        *(volatile int32_t *)&p.c->pub_level = j;
-        *(volatile int32_t *)&p.c->gate_cmd = cmd;
-        __threadfence();
-        atomicExch(&p.c->gate, ((unsigned long long)p.epoch << 32) | (unsigned long long)(seen + 1));
-    }
-    seen++;
+    if (threadIdx.x == 0) *(volatile unsigned long long *)&p.c->gate = word;
     __syncthreads();
 }
 
@@ -1346,6 +1464,21 @@ __device__ __forceinline__ void clear_frontier_bits(const KParams &p, const Shar
     }
 }
 
+// CTA 0: copies level j's counters from its shared memory to device memory,
+// where the CTAs it is about to wake read them.
+__device__ __forceinline__ void publish_counters(const KParams &p, const Shared &sh, int j) {
+    const int cs = j % 3;
+    const Ctrs &G = sh.cv[0], &S = sh.cv[1];
+    for (int q = threadIdx.x; q < p.S; q += kThreads)
+        G.fl[cs * kMaxStates + q] = S.fl[cs * kMaxStates + q];
+    for (int g = threadIdx.x; g < p.n_groups; g += kThreads)
+        G.mf[cs * G.mstride + g] = S.mf[cs * S.mstride + g];
+    if (threadIdx.x == 0) {
+        G.rows[cs] = S.rows[cs];
+        G.srows[cs] = S.srows[cs];
+    }
+}
+
 // CTA 0: sets the frontier bits of level j (list range [vstart, vnext)) in
 // slot j % 3, for a level that the whole grid is about to run.
 __device__ __forceinline__ void set_frontier_bits(const KParams &p, const Shared &sh, int j) {
@@ -1471,6 +1604,31 @@ __device__ void solo_answer(const KParams &p, const Shared &sh, bool f_live, int
     while (n2 < T) n2 <<= 1;
     for (int i = T + threadIdx.x; i < n2; i += kThreads) buf[i] = INT32_MAX;
     __syncthreads();
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    if (T <= 32) {
+        // one warp: a bitonic network over the lanes' registers
+        if (warp == 0) {
+            int32_t v = buf[lane];
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    const int32_t o = __shfl_xor_sync(kFull, v, jj);
+                    const bool lower = (lane & jj) == 0, ascending = (lane & k) == 0;
+                    v = lower == ascending ? min(v, o) : max(v, o);
+                }
+            }
+            const int32_t prev = __shfl_up_sync(kFull, v, 1);
+            const bool keep = v != INT32_MAX && (lane == 0 || prev != v);
+            const unsigned bm = __ballot_sync(kFull, keep);
+            const long long pos = __popc(bm & lanemask_lt());
+            int32_t *dst = p.out_list_small ? p.out_list_small : p.out_list;
+            if (keep && dst && pos < p.capacity) dst[pos] = v;
+            if (lane == 0) p.c->answer_count = __popc(bm);
+        }
+        return;
+    }
     for (int k = 2; k <= n2; k <<= 1) {
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
             for (int i = threadIdx.x; i < n2; i += kThreads) {
@@ -1486,8 +1644,6 @@ __device__ void solo_answer(const KParams &p, const Shared &sh, bool f_live, int
             __syncthreads();
         }
     }
-    const unsigned lane = lane_id();
-    const int warp = threadIdx.x >> 5;
     long long run = 0;
     for (int base = 0; base < n2; base += kThreads) {
         const int i = base + threadIdx.x;
@@ -1503,7 +1659,8 @@ __device__ void solo_answer(const KParams &p, const Shared &sh, bool f_live, int
             tot += c;
         }
         const long long pos = run + before + __popc(bm & lanemask_lt());
-        if (keep && p.out_list && pos < p.capacity) p.out_list[pos] = v;
+        int32_t *dst = p.out_list_small ? p.out_list_small : p.out_list;
+        if (keep && dst && pos < p.capacity) dst[pos] = v;
         run += tot;
         __syncthreads();
     }
@@ -1511,19 +1668,19 @@ __device__ void solo_answer(const KParams &p, const Shared &sh, bool f_live, int
 }
 
 // CTA 0, thread 0, at the end of a successful query: the summary to the
-// host-mapped result (every field is thread 0's own earlier write).
-__device__ __forceinline__ void write_result(const KParams &p) {
+// host-mapped result (the answer count is thread 0's own earlier write).
+__device__ __forceinline__ void write_result(const KParams &p, const Shared &sh, bool small) {
     if (!p.result || threadIdx.x != 0) return;
-    const volatile Counters *c = p.c;
     QueryResult *r = p.result;
-    r->levels = c->levels;
-    r->visited = c->visited;
-    r->expanded = c->expanded;
-    r->product_edges = c->product_edges;
-    r->push_bytes = c->push_bytes;
-    r->push_units = c->push_units;
-    r->pull_units = c->pull_units;
-    r->answer_count = c->answer_count;
+    r->small = small ? 1 : 0;
+    r->levels = sh.stats[kStLevels];
+    r->visited = sh.stats[kStVisited];
+    r->expanded = sh.stats[kStExpanded];
+    r->product_edges = sh.stats[kStProductEdges];
+    r->push_bytes = sh.stats[kStPushBytes];
+    r->push_units = sh.stats[kStPushUnits];
+    r->pull_units = sh.stats[kStPullUnits];
+    r->answer_count = *(volatile long long *)&p.c->answer_count;
     r->epoch = p.epoch;  // the host reads the summary after the stream has synchronised
 }
 
@@ -1567,24 +1724,25 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
     bool from_gate_final = false;
     int j = 0, plan = kPlanStop;
     if (lead) {
-        // prologue on CTA 0: counters of all slots cleared; P = F_0 = Q_S x {v_s}
-        // with the level-0 lists, edge mass and long rows of every start state
+        // prologue on CTA 0: the device-memory counters of all slots cleared
+        // (its shared-memory ones were cleared with the tables); P = F_0 =
+        // Q_S x {v_s} with the level-0 lists, edge mass and long rows of every
+        // start state, counted in shared memory (CTA 0 starts alone)
+        Counters *c = p.c;
         for (int i = threadIdx.x; i < 3 * kMaxGroups; i += kThreads) p.mf[i] = 0;
+        for (int i = threadIdx.x; i < 3 * kMaxStates; i += kThreads) (&c->fl_count[0][0])[i] = 0;
+        if (threadIdx.x < 3) {
+            const int k = threadIdx.x;
+            c->rows_packed[k] = c->lvl_bytes[k] = c->lvl_edges[k] = c->srows_count[k] = 0;
+            c->claim_chunk[k] = c->claim_item[k] = c->claim_pull[k] = 0;
+        }
         if (threadIdx.x == 0) {
-            Counters *c = p.c;
-            for (int k = 0; k < 3; k++) {
-                for (int q = 0; q < kMaxStates; q++) c->fl_count[k][q] = 0;
-                c->rows_packed[k] = c->lvl_bytes[k] = c->lvl_edges[k] = 0;
-                c->claim_chunk[k] = c->claim_item[k] = c->claim_pull[k] = 0;
-            }
-            c->levels = c->visited = c->expanded = c->product_edges = c->push_bytes = 0;
-            c->push_units = c->pull_units = c->answer_count = 0;
+            c->answer_count = 0;
             c->parked = 0;
         }
-        __syncthreads();
         if (threadIdx.x < 32) {
-            // CTA 0 starts alone: like every solo level, no frontier bits
-            LevelCtx L0{0, p.VL, sh.vnext, nullptr, p.rows[0], p.cmap[0], s_acc};
+            // like every solo level, no frontier bits
+            LevelCtx L0{0, &sh.cv[1], p.VL, sh.vnext, nullptr, s_acc};
             const uint32_t swi = (uint32_t)p.source >> 6;
             const uint64_t sbit = 1ull << (p.source & 63);
             uint64_t sm = p.start_mask;
@@ -1597,21 +1755,22 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             }
             __syncwarp();
             if (threadIdx.x == 0) {
-                p.c->lvl_bytes[0] = s_acc[0];
-                p.c->lvl_edges[0] = s_acc[1];
+                sh.cv[1].bytes[0] = s_acc[0];
+                sh.cv[1].edges[0] = s_acc[1];
                 s_acc[0] = s_acc[1] = 0;
             }
             for (int g = threadIdx.x; g < p.n_groups; g += 32) {
-                p.mf[g] = sh.s_mf[g];
+                sh.cv[1].mf[g] = sh.s_mf[g];
                 sh.s_mf[g] = 0;
             }
         }
         __syncthreads();
         if (p.trace && threadIdx.x == 0)
             p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
-        level_advance(p, 0, sh, true);
+        level_advance(p, 0, sh, true, true);
         plan = level_plan(p, 0, sh, true);
     }
+    bool cur_smem = lead;  // level j's counters are in CTA 0's shared memory
     bool prev_grid = false;  // level j-1 ran on the grid (its frontier bits exist)
     unsigned long long parked_expected = 0;  // CTA 0: parkings so far
     bool park_pending = false;               // CTA 0: the last parking may be incomplete
@@ -1624,6 +1783,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             level_join(p, j, sh);
             grid = true;
             prev_grid = false;
+            cur_smem = false;
             if (cmd == kGateFinal) {
                 from_gate_final = true;
                 break;
@@ -1649,6 +1809,8 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             if (park_pending && !park_wait(p, parked_expected)) return;
             park_pending = false;
             set_frontier_bits(p, sh, j);  // level j may pull: its frontier needs its bits
+            publish_counters(p, sh, j);
+            cur_smem = false;
             gate_release(p, sh, seen, kGateLevel, j);
             grid = true;
         } else if (!grid && park_pending) {
@@ -1669,8 +1831,9 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             p.trace[(size_t)j * kTraceFields + 7] = sh.lvl[0];
         }
         expand_phase(p, j, sh, s_gsf, &s_claim, s_acc, grid ? (int)blockIdx.x : 0,
-                     grid ? (int)gridDim.x : 1, grid, grid && prev_grid);
+                     grid ? (int)gridDim.x : 1, grid, grid && prev_grid, cur_smem);
         prev_grid = grid;
+        cur_smem = !grid;
         trace_put(p, j, 1, global_timer_ns());
         if (grid) {
             if (!grid_barrier(p.c)) return;
@@ -1681,7 +1844,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         }
         trace_put(p, j, 2, global_timer_ns());
         j++;
-        level_advance(p, j, sh, lead);
+        level_advance(p, j, sh, lead, cur_smem);
         plan = level_plan(p, j, sh, lead);
     }
     if (p.trace && lead && threadIdx.x == 0)
@@ -1696,6 +1859,9 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         __syncthreads();
         solo_end = true;
     } else if (!grid) {
+        // the grid joins the answer sweep: it needs level j's counters too
+        if (park_pending && !park_wait(p, parked_expected)) return;
+        publish_counters(p, sh, j);
         gate_release(p, sh, seen, kGateFinal, j);
         grid = true;
     }
@@ -1705,7 +1871,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         final_write(p, &s_claim);
         clear_state(p, sh, false, f_live, j, (int)blockIdx.x, (int)gridDim.x);
     }
-    if (lead) write_result(p);
+    if (lead) write_result(p, sh, solo_end);
     if (p.trace && lead && threadIdx.x == 0)
         p.trace[(size_t)(p.trace_cap) * kTraceFields + 3] = global_timer_ns();
 }
@@ -1714,9 +1880,9 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
 
 struct QueryWorkspace : WorkspaceBase {
     int S_cap = 0;
-    long long row_cap = 0, chunk_cap = 0;
+    long long row_cap = 0, chunk_cap = 0, srow_cap = 0;
     int32_t n = 0, W = 0;
-    DevBuf P, F[3], VL, rows[3], cmap[3], mf, fin, ctr, tables, out_list, trace;
+    DevBuf P, F[3], VL, rows[3], cmap[3], srl[3], mf, fin, ctr, tables, out_list, trace;
     void *staging = nullptr;  // pinned host: tables upload + counters download
     size_t staging_bytes = 0;
     QueryResult *result_dev = nullptr;  // device address of the summary slot of staging
@@ -1731,6 +1897,36 @@ struct QueryWorkspace : WorkspaceBase {
 };
 
 constexpr size_t kTablesBytes = 256 * 1024;
+
+// Per host thread: pinned host memory, mapped into the device, that the
+// kernel writes host answers to, and the last such answer.
+struct HostAnswer {
+    int32_t *h = nullptr, *d = nullptr;
+    size_t cap = 0;
+    int64_t count = 0;
+    bool valid = false;
+    ~HostAnswer() {
+        if (h) cudaFreeHost(h);
+    }
+    bool reserve(size_t n) {
+        if (cap >= n) return true;
+        if (h) cudaFreeHost(h);
+        h = d = nullptr;
+        cap = 0;
+        void *hp = nullptr, *dp = nullptr;
+        if (cudaHostAlloc(&hp, sizeof(int32_t) * n, cudaHostAllocMapped | cudaHostAllocPortable) !=
+                cudaSuccess ||
+            cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess) {
+            if (hp) cudaFreeHost(hp);
+            return false;
+        }
+        h = static_cast<int32_t *>(hp);
+        d = static_cast<int32_t *>(dp);
+        cap = n;
+        return true;
+    }
+};
+thread_local HostAnswer tl_answer;
 // staging: tables | counters (read back after a failure) | summary
 constexpr size_t kResultOffset = (kTablesBytes + sizeof(Counters) + 63) & ~size_t(63);
 
@@ -1776,22 +1972,24 @@ rpq_status get_launch_shape(int device, size_t smem, int *grid) {
 }
 
 rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long row_cap,
-                    long long chunk_cap) {
+                    long long chunk_cap, long long srow_cap) {
     const int64_t W = ((int64_t)g->n + 63) / 64;
     const size_t bits = sizeof(uint64_t) * (size_t)S_cap * W;
     const size_t fl = sizeof(int32_t) * (size_t)S_cap * g->n;
     ws->S_cap = S_cap;
     ws->row_cap = row_cap;
     ws->chunk_cap = chunk_cap;
+    ws->srow_cap = srow_cap;
     ws->n = g->n;
     ws->W = (int32_t)W;
     bool ok = ws->P.alloc(bits) && ws->mf.alloc(sizeof(unsigned long long) * 3 * kMaxGroups) &&
               ws->fin.alloc(sizeof(long long) * 152 * 64) && ws->ctr.alloc(sizeof(Counters)) &&
-              ws->tables.alloc(kTablesBytes) && ws->out_list.alloc(sizeof(int32_t) * (size_t)g->n) &&
-              ws->VL.alloc(fl);
+              ws->tables.alloc(kTablesBytes) && ws->VL.alloc(fl) &&
+              ws->out_list.alloc(sizeof(int32_t) * (size_t)g->n);
     for (int k = 0; k < 3 && ok; k++)
         ok = ws->F[k].alloc(bits) && ws->rows[k].alloc(sizeof(Row) * (size_t)row_cap) &&
-             ws->cmap[k].alloc(sizeof(int32_t) * (size_t)chunk_cap);
+             ws->cmap[k].alloc(sizeof(int32_t) * (size_t)chunk_cap) &&
+             ws->srl[k].alloc(sizeof(int4) * (size_t)srow_cap);
     if (!ok) return fail(RPQ_ERR_OOM, "query workspace (%d states)", S_cap);
     // the kernel expects P and F all-zero on entry and leaves them so
     RPQ_CUDA_TRY(cudaMemset(ws->ctr.p, 0, sizeof(Counters)));
@@ -1809,12 +2007,14 @@ rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long
 }
 
 std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, long long row_need,
-                                           long long chunk_need, rpq_status *st) {
+                                           long long chunk_need, long long srow_need,
+                                           rpq_status *st) {
     {
         std::lock_guard<std::mutex> lk(g->ws_mu);
         for (size_t i = 0; i < g->ws_free.size(); i++) {
             auto *w = dynamic_cast<QueryWorkspace *>(g->ws_free[i].get());
-            if (w && w->S_cap >= S && w->row_cap >= row_need && w->chunk_cap >= chunk_need) {
+            if (w && w->S_cap >= S && w->row_cap >= row_need && w->chunk_cap >= chunk_need &&
+                w->srow_cap >= srow_need) {
                 std::unique_ptr<QueryWorkspace> r(static_cast<QueryWorkspace *>(g->ws_free[i].release()));
                 g->ws_free.erase(g->ws_free.begin() + i);
                 *st = RPQ_OK;
@@ -1825,10 +2025,11 @@ std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, long long row_ne
     std::unique_ptr<QueryWorkspace> w(new QueryWorkspace());
     int S_cap = 4;
     while (S_cap < S) S_cap *= 2;
-    long long rc = 1024, cc = 4096;
+    long long rc = 1024, cc = 4096, sc = 4096;
     while (rc < row_need) rc *= 2;
     while (cc < chunk_need) cc *= 2;
-    *st = ws_alloc(w.get(), g, S_cap, rc, cc);
+    while (sc < srow_need) sc *= 2;
+    *st = ws_alloc(w.get(), g, S_cap, rc, cc, sc);
     if (*st != RPQ_OK) return nullptr;
     return w;
 }
@@ -1843,7 +2044,7 @@ struct Tables {
     std::vector<QGroup> groups;
     std::vector<QUnit> units;
     std::vector<int32_t> t_unit, t_state, u_group;
-    long long row_need = 0, chunk_need = 0;
+    long long row_need = 0, chunk_need = 0, srow_need = 0;
 };
 
 rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
@@ -1894,6 +2095,10 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
         // rows of one group are at most the long rows of its adjacency
         t->row_need += g->long_rows[G.d] + 1;
         t->chunk_need += g->long_chunks[G.d] + 1;
+        // ... and its listed short rows (hypersparse adjacencies only) at
+        // most the short rows of its adjacency
+        if (g->adj[G.d].fmt == ADJ_HYPER) t->srow_need += g->short_rows[G.d];
+        t->srow_need += 1;
     }
     for (size_t u = 0; u < t->units.size(); u++) {
         QUnit &U = t->units[u];
@@ -1912,7 +2117,9 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
 // Appends one JSON line per query: the kernel's phase times and, per level,
 // block 0's timestamps (ns, relative to the kernel start) with the frontier
 // size, the number of push / pull units, whether the level ran on the
-// whole grid (1) or on CTA 0 alone (0), and the push-model bytes of its rows.
+// whole grid (1) or on CTA 0 alone (0), the push-model bytes of its rows,
+// block 0's end of the long-row and short-row phases, and the first and last
+// CTA's end of the level.
 void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int levels,
                  cudaStream_t st) {
     std::vector<unsigned long long> h((size_t)kTraceFields * levels), gs(kTraceFields);
@@ -1933,8 +2140,9 @@ void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int le
     for (int j = 0; j < levels; j++) {
         const unsigned long long *r = &h[(size_t)j * kTraceFields];
         if (r[0] == 0) break;
-        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu, %llu, %llu]", j ? ", " : "",
-                rel(r[0]), rel(r[1]), rel(r[2]), r[3], r[4], r[5], r[6], r[7]);
+        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu, %llu, %llu, %lld, %lld, %lld, %lld]",
+                j ? ", " : "", rel(r[0]), rel(r[1]), rel(r[2]), r[3], r[4], r[5], r[6], r[7],
+                rel(r[8]), rel(r[9]), rel(r[10] ? ~r[10] : 0), rel(r[11]));
     }
     fprintf(f, "]}\n");
     fclose(f);
@@ -2000,9 +2208,18 @@ float env_float(const char *name, float dflt) {
 // fits in `capacity`); out_bits_dev receives the answer bitset if non-null.
 rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
                      int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
-                     int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream) {
+                     int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
+                     bool host_list) {
     return run_query_slot(g, a, source, max_levels, out_list_dev, capacity, out_bits_dev,
-                          out_host_list, stats, count, stream, 1);
+                          out_host_list, stats, count, stream, 1, host_list);
+}
+
+rpq_status last_host_answer(const int32_t **answer, int64_t *count) {
+    if (!answer || !count) return fail(RPQ_ERR_INVALID, "null argument");
+    if (!tl_answer.valid) return fail(RPQ_ERR_INVALID, "this thread has no host answer");
+    *answer = tl_answer.h;
+    *count = tl_answer.count;
+    return RPQ_OK;
 }
 
 // As run_query, on 1/grid_div of the persistent grid, so that grid_div
@@ -2010,8 +2227,10 @@ rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t m
 rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
                           int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
                           int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
-                          int grid_div) {
+                          int grid_div, bool host_list) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool want_host = !out_list_dev && (host_list || out_host_list);
+    tl_answer.valid = false;  // a host answer lives until this thread's next query
     if (source < 0 || source >= g->n)
         return fail(RPQ_ERR_INVALID, "source %d outside [0, %d)", source, g->n);
     if (max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
@@ -2019,7 +2238,8 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     Tables t;
     rpq_status s = build_tables(g, a, &t);
     if (s != RPQ_OK) return s;
-    std::unique_ptr<QueryWorkspace> ws = ws_acquire(g, a.S, t.row_need, t.chunk_need, &s);
+    std::unique_ptr<QueryWorkspace> ws =
+        ws_acquire(g, a.S, t.row_need, t.chunk_need, t.srow_need, &s);
     if (!ws) return s;
     uint8_t *hs = static_cast<uint8_t *>(ws->staging);
     KParams p{};
@@ -2055,9 +2275,11 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
         p.F[k] = ws->F[k].as<uint64_t>();
         p.rows[k] = ws->rows[k].as<Row>();
         p.cmap[k] = ws->cmap[k].as<int32_t>();
+        p.srl[k] = ws->srl[k].as<int4>();
     }
     p.row_cap = ws->row_cap;
     p.chunk_cap = ws->chunk_cap;
+    p.srow_cap = ws->srow_cap;
     p.mf = ws->mf.as<unsigned long long>();
     p.fin_sums = ws->fin.as<long long>();
     p.c = ws->ctr.as<Counters>();
@@ -2076,8 +2298,16 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     if (out_list_dev) {
         p.out_list = out_list_dev;
         p.capacity = capacity;
-    } else if (out_host_list) {
+    } else if (want_host) {
+        // a small answer is written by the kernel straight to this thread's
+        // pinned host buffer (over the host link); a large one goes to device
+        // memory and comes over by one copy after the kernel
+        if (!tl_answer.reserve((size_t)g->n)) {
+            ws_release(g, std::move(ws));
+            return fail(RPQ_ERR_OOM, "pinned answer buffer (%d entries)", g->n);
+        }
         p.out_list = ws->out_list.as<int32_t>();
+        p.out_list_small = tl_answer.d;
         p.capacity = g->n;
     } else {
         p.out_list = nullptr;
@@ -2115,9 +2345,10 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     ws->dirty = false;
     *count = hr->answer_count;
     const bool copy_list = out_host_list && !out_list_dev && *count <= capacity && *count > 0;
+    const int64_t host_bytes = want_host ? 4 * *count : 0;
     if (stats) {
         stats->h2d_bytes = (int64_t)tab_bytes;
-        stats->d2h_bytes = (int64_t)sizeof(QueryResult) + (copy_list ? 4 * *count : 0);
+        stats->d2h_bytes = (int64_t)sizeof(QueryResult) + host_bytes;
         stats->levels = hr->levels;
         stats->visited_pairs = hr->visited;
         stats->expanded_pairs = hr->expanded;
@@ -2130,11 +2361,16 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
         if (cudaEventElapsedTime(&ms, ws->ev0, ws->ev1) != cudaSuccess) ms = -1.0f;
         stats->device_ms = ms;
     }
-    if (copy_list) {
-        RPQ_CUDA_TRY(cudaMemcpyAsync(out_host_list, ws->out_list.p, sizeof(int32_t) * (*count),
-                                     cudaMemcpyDeviceToHost, st));
-        RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (want_host) {
+        if (!hr->small && *count > 0) {
+            RPQ_CUDA_TRY(cudaMemcpyAsync(tl_answer.h, ws->out_list.p, sizeof(int32_t) * (*count),
+                                         cudaMemcpyDeviceToHost, st));
+            RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        tl_answer.count = *count;
+        tl_answer.valid = true;
     }
+    if (copy_list) memcpy(out_host_list, tl_answer.h, sizeof(int32_t) * (size_t)(*count));
     if (trace_path)
         write_trace(trace_path, ws.get(), a.S, source,
                     (int)std::min<long long>(hr->levels + 2, kTraceLevels), st);
@@ -2290,11 +2526,12 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     const size_t bits = sizeof(uint64_t) * (size_t)a.S * W;
     const size_t fl = sizeof(int32_t) * (size_t)a.S * g->n;
     const size_t x_P = take(bits);
-    size_t x_F[3], x_rows[3], x_cmap[3];
+    size_t x_F[3], x_rows[3], x_cmap[3], x_srl[3];
     for (int k = 0; k < 3; k++) x_F[k] = take(bits);
     const size_t x_VL = take(fl);
     for (int k = 0; k < 3; k++) x_rows[k] = take(sizeof(Row) * (size_t)t.row_need);
     for (int k = 0; k < 3; k++) x_cmap[k] = take(sizeof(int32_t) * (size_t)t.chunk_need);
+    for (int k = 0; k < 3; k++) x_srl[k] = take(sizeof(int4) * (size_t)t.srow_need);
     if (off > RPQ_NOALLOC_SCRATCH_BYTES)
         return fail(RPQ_ERR_INVALID,
                     "query needs %zu bytes of scratch; rpq_query_noalloc holds %llu "
@@ -2339,9 +2576,11 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
         p.F[k] = reinterpret_cast<uint64_t *>(base + x_F[k]);
         p.rows[k] = reinterpret_cast<Row *>(base + x_rows[k]);
         p.cmap[k] = reinterpret_cast<int32_t *>(base + x_cmap[k]);
+        p.srl[k] = reinterpret_cast<int4 *>(base + x_srl[k]);
     }
     p.row_cap = t.row_need;
     p.chunk_cap = t.chunk_need;
+    p.srow_cap = t.srow_need;
     p.mf = reinterpret_cast<unsigned long long *>(base + x_mf);
     p.fin_sums = reinterpret_cast<long long *>(base + x_fin);
     p.c = reinterpret_cast<Counters *>(base + x_ctr);

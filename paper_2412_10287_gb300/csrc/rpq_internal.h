@@ -72,11 +72,14 @@ rpq_status device_exclusive_scan(const T *in, int64_t *out, int64_t n, int64_t *
 // Single query (query.cu).  See run_query there for the output contract.
 rpq_status run_query(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
                      int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
-                     int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream);
+                     int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
+                     bool host_list = false);
 rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
                           int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
                           int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
-                          int grid_div);
+                          int grid_div, bool host_list = false);
+// The calling thread's last host answer (run_query with a host list).
+rpq_status last_host_answer(const int32_t **answer, int64_t *count);
 
 // Sorted vertex lists of `count` answer bitsets (row i at bits + i * words32
 // uint32 words) into out (host or device, capacity entries); offsets

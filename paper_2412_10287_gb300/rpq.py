@@ -31,7 +31,8 @@ EXPORTED = (
     "rpq_set_allocator", "rpq_graph_load", "rpq_graph_free", "rpq_graph_info", "rpq_graph_export",
     "rpq_graph_autotune",
     "rpq_nfa_compile", "rpq_nfa_from_transitions", "rpq_nfa_free", "rpq_nfa_info",
-    "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_query_noalloc",
+    "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_last_answer",
+    "rpq_query_noalloc",
     "rpq_query_bitset",
     "rpq_query_batch", "rpq_serve_create", "rpq_serve_submit", "rpq_serve_poll",
     "rpq_serve_drain", "rpq_serve_stats_get", "rpq_serve_destroy", "rpq_last_error",
@@ -102,6 +103,7 @@ def lib():
             "rpq_nfa_accepts": [p, p, i32, p],
             "rpq_nfa_reverse": [p, pp],
             "rpq_query": [p, p, i32, i32, p, i64, p, p, p],
+            "rpq_last_answer": [p, p],
             "rpq_query_noalloc": [p, p, i32, i32, p, i64, p, p],
             "rpq_query_bitset": [p, p, i32, i32, p, p, p, p],
             "rpq_query_batch": [p, i32, p, p, i32, p, p, i64, p, p],
@@ -347,12 +349,15 @@ def rpq_query(g: Graph, nfa: Nfa, source: int, max_levels: int = 0, out=None, st
     cnt = ctypes.c_int64()
     sp = ctypes.byref(st) if st is not None else None
     if out is None:
-        # an answer has at most n vertices: one call, never a second pass
-        buf = np.empty(g.n, np.int32)
-        _check(lib().rpq_query(g.h, nfa.h, int(source), int(max_levels), _ptr(buf), g.n,
-                               ctypes.byref(cnt), sp, _stream_handle(stream)))
-        c = int(cnt.value)
-        res = buf[:c].copy() if 4 * c < g.n else buf[:c]
+        # no buffer: the library keeps the answer in pinned host memory
+        # (written there by the kernel); one copy into the result array
+        _check(lib().rpq_query(g.h, nfa.h, int(source), int(max_levels), None, 0,
+                               ctypes.byref(cnt), sp, _stream_handle(stream)),
+               allow=(RPQ_ERR_CAPACITY,))
+        ptr, n = ctypes.POINTER(ctypes.c_int32)(), ctypes.c_int64()
+        _check(lib().rpq_last_answer(ctypes.byref(ptr), ctypes.byref(n)))
+        res = (np.ctypeslib.as_array(ptr, shape=(n.value,)).copy() if n.value
+               else np.empty(0, np.int32))
     else:
         _check(lib().rpq_query(g.h, nfa.h, int(source), int(max_levels), _ptr(out), out.numel(),
                                ctypes.byref(cnt), sp, _stream_handle(stream)))

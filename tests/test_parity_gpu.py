@@ -336,12 +336,47 @@ def test_solo_levels_and_workspace_reuse(solo, pull_mode, monkeypatch):
         check_counters(st, og.ssr(same, s)["counters"])
     for (t, s), o in zip(jobs[:5], exp[:5]):
         assert gpu_regex(gg, t, 4, s).tolist() == o["answer"].tolist(), (t, s)
-    # bitset output and a level cap go through the grid-wide answer sweep
-    for (t, s) in jobs[:4]:
-        bits = np.zeros((g.n + 63) // 64, np.uint64)
-        R.rpq_query_bitset(gg, R.rpq_nfa_compile(t, 4), s, out=bits)
-        ids = np.nonzero(np.unpackbits(bits.view(np.uint8), bitorder="little"))[0]
-        assert ids.tolist() == og.ssr(oracle_compile(t, 4), s)["answer"].tolist()
-        k = 2
-        assert gpu_regex(gg, t, 4, s, k).tolist() == \
-            og.ssr(oracle_compile(t, 4), s, k)["answer"].tolist()
+    # bitset outputs go through the grid-wide answer sweep, also when a level
+    # cap stops the traversal with a non-empty frontier; list outputs under a
+    # cap; then the first queries again on the reused workspaces
+    for (t, s) in jobs[:7]:
+        for k in (0, 1, 2):
+            exp_k = og.ssr(oracle_compile(t, 4), s, k)["answer"].tolist()
+            bits = np.zeros((g.n + 63) // 64, np.uint64)
+            R.rpq_query_bitset(gg, R.rpq_nfa_compile(t, 4), s, max_levels=k, out=bits)
+            ids = np.nonzero(np.unpackbits(bits.view(np.uint8), bitorder="little"))[0]
+            assert ids.tolist() == exp_k, (t, s, k)
+            assert gpu_regex(gg, t, 4, s, k).tolist() == exp_k, (t, s, k)
+    for (t, s), o in zip(jobs[:5], exp[:5]):
+        assert gpu_regex(gg, t, 4, s).tolist() == o["answer"].tolist(), (t, s)
+
+
+def test_last_answer_two_call_pattern():
+    """A host buffer that is too small gets RPQ_ERR_CAPACITY with the full
+    count; rpq_last_answer then hands over the whole answer without a second
+    traversal.  After a query into device memory there is no host answer."""
+    import ctypes
+
+    import torch
+
+    g = W.rmat_graph(13, 60000, 4, seed=81)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    nfa = R.rpq_nfa_compile("(0|1)*", 4)
+    srcs = W.below(82, 1, 6, g.n).tolist()
+    for s in srcs:
+        exp = og.ssr(oracle_compile("(0|1)*", 4), s)["answer"]
+        small = np.zeros(1, np.int32)
+        cnt = ctypes.c_int64()
+        st = R.lib().rpq_query(gg.h, nfa.h, s, 0, R._ptr(small), 1, ctypes.byref(cnt), None, None)
+        assert st == (R.RPQ_OK if exp.size <= 1 else R.RPQ_ERR_CAPACITY)
+        assert cnt.value == exp.size
+        ptr, n = ctypes.POINTER(ctypes.c_int32)(), ctypes.c_int64()
+        assert R.lib().rpq_last_answer(ctypes.byref(ptr), ctypes.byref(n)) == R.RPQ_OK
+        got = np.ctypeslib.as_array(ptr, shape=(n.value,)).copy() if n.value else np.empty(0)
+        assert got.tolist() == exp.tolist()
+        assert R.rpq_query(gg, nfa, s).tolist() == exp.tolist()
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    R.rpq_query(gg, nfa, srcs[0], out=out)
+    ptr, n = ctypes.POINTER(ctypes.c_int32)(), ctypes.c_int64()
+    assert R.lib().rpq_last_answer(ctypes.byref(ptr), ctypes.byref(n)) == R.RPQ_ERR_INVALID
