@@ -268,9 +268,9 @@ def autotune(R, gg, g, name):
 
     tpl = W.TEMPLATES_KB if name == "kb20m" else W.TEMPLATES_SMALL
     sample = W.make_queries(g, tpl, 4, seed=99, zipf_s=1.1 if name == "kb20m" else 1.0)
-    alpha, mn = R.rpq_graph_autotune(gg, [R.rpq_nfa_compile(q.regex, g.n_labels) for q in sample],
-                                     [q.source for q in sample])
-    return {"pull_alpha": alpha, "pull_min": mn,
+    alpha, mn, solo = R.rpq_graph_autotune(gg, [R.rpq_nfa_compile(q.regex, g.n_labels)
+                                                 for q in sample], [q.source for q in sample])
+    return {"pull_alpha": alpha, "pull_min": mn, "solo_mass": solo,
             "sample": f"{len(sample)} queries of the same templates, seed 99"}
 
 

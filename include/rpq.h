@@ -108,19 +108,23 @@ rpq_status rpq_graph_info(const rpq_graph *g, int32_t label, int32_t *n_vertices
 rpq_status rpq_graph_export(const rpq_graph *g, int32_t label, int32_t inverse,
                             int64_t *offsets, int32_t *neighbours, int64_t capacity);
 
-/* Autotuner for the direction choice of single queries (push for sparse
- * frontiers, pull for dense ones; the paper's section 5.1 switches between
- * its two formulations at an empirically chosen nnz, here the threshold is
- * measured).  Runs the n sample queries (nfas[i] from sources[i]) under every
- * candidate setting -- pull when the frontier's edge mass x alpha exceeds the
- * in-adjacency's edges + rows, alpha in {0 (push only), 1, 2, 4, 8, 16, 64},
- * and the frontier holds at least min_pull in {64, 256, 2048} pairs -- keeps
+/* Autotuner for single queries.  First the direction choice (push for
+ * sparse frontiers, pull for dense ones; the paper's section 5.1 switches
+ * between its two formulations at an empirically chosen nnz, here the
+ * threshold is measured): runs the n sample queries (nfas[i] from
+ * sources[i]) under every candidate setting -- pull when the frontier's edge
+ * mass x alpha exceeds the in-adjacency's edges + rows, alpha in {0 (push
+ * only), 1, 2, 4, 8, 16, 64}, and the frontier holds at least min_pull in
+ * {64, 256, 2048} pairs.  Then, with that setting, the size below which a
+ * level runs on one CTA with no grid barrier: push edge mass solo_mass in
+ * {-1 (never), 512, 2048, 8192} (with solo_mass / 8 frontier items).  Keeps
  * the fastest by device time, stores it in the graph for later rpq_query
- * calls (the environment variables RPQ_PULL_ALPHA / RPQ_PULL_MIN still
- * override) and reports it.  Results never depend on the setting. */
+ * calls (the environment variables RPQ_PULL_ALPHA, RPQ_PULL_MIN,
+ * RPQ_SOLO_MASS and RPQ_SOLO_ITEMS still override) and reports it; any out
+ * pointer may be NULL.  Results never depend on the setting. */
 rpq_status rpq_graph_autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
                               const int32_t *sources, float *alpha_out, int32_t *min_pull_out,
-                              void *stream);
+                              int32_t *solo_mass_out, void *stream);
 
 /* ---------------------------------------------------------- automaton -- */
 

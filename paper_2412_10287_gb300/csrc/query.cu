@@ -18,14 +18,18 @@
 //     pull     for every w not in P[q'] with in-edges of direction d: one
 //              in-neighbour u with X_{d,q'}[u] = OR_{q: q -d-> q'} M_j[q][u]
 //              suffices (early exit); then the same atomicOr discovery.
-//   A discovered pair is appended to the frontier list of q', its bit set in
-//   F_{j+1}, and the rows it will expand are measured: their edge mass steers
-//   the next push/pull choice (a direction-optimising BFS: the push-pull
-//   optimisation the paper's conclusion names); rows of >= kWarpRow edges go
-//   to a chunk list that every warp of the grid draws 128-edge chunks from,
-//   shorter rows are expanded by a CTA-wide scan-based gather.
-//   decide j+1 (every CTA, same data): stop when M_{j+1} is empty or the level
-//   cap is reached; else pick push or pull per (d, q').
+//   A discovered pair is appended to the visited list of q', its bit set in
+//   F_{j+1} (on grid levels: only pull reads it), and the rows it will
+//   expand are measured: their edge mass steers the next push/pull choice
+//   (a direction-optimising BFS: the push-pull optimisation the paper's
+//   conclusion names); rows of >= kWarpRow edges go to a chunk list that
+//   every warp draws 128-edge chunks from; shorter rows are expanded by a
+//   CTA-wide scan-based gather, from a list of them made at discovery
+//   (where finding a row again is costly or mostly finds nothing) or from
+//   the frontier list and the row offsets.
+//   plan j+1 (every working CTA, same data): stop when M_{j+1} is empty or
+//   the level cap is reached; else pick push or pull per (d, q') and
+//   whether CTA 0 runs the level alone.
 //
 // The answer F x P is either swept from P by the grid or, when it is small,
 // gathered from the final states' lists and sorted by CTA 0.  The kernel
@@ -66,6 +70,8 @@ struct QGroup {
     int32_t q, d;
     uint64_t tmask;
     int32_t t_first, t_count;  // slots in the target table: (unit, q') pairs
+    int32_t listed;            // its short rows go to the level's short-row list
+    int32_t pad;
 };
 // (direction d, target state q') with the source states {q : q -d-> q'}.
 struct QUnit {
@@ -229,7 +235,8 @@ struct Shared {
     uint64_t *tpush;    // push-mode targets of each group (decided per level)
     long long *nsrow;   // [2]: [0] short rows listed for the current level
     long long *dpref;   // [n_groups + 1] prefix of frontier items over dense push groups
-    uint8_t *gdense;    // [n_groups] the group's adjacency has dense offsets
+    uint8_t *gdense;    // [n_groups] short rows found from the frontier list and dense offsets
+                        // (else listed at discovery)
     const int32_t **gnbr;
     int32_t *gq, *gd, *gtpop;
     int32_t *gt_first, *gt_count;
@@ -370,7 +377,9 @@ __device__ void load_tables(const KParams &p, const Shared &sh) {
         sh.gq[g] = G.q;
         sh.gd[g] = G.d;
         sh.gnbr[g] = p.adj[G.d].nbr;
-        sh.gdense[g] = p.adj[G.d].fmt == ADJ_DENSE ? 1 : 0;
+        // only a dense adjacency has offsets to find a row by (an empty one
+        // has none: its groups take the listed path, which lists nothing)
+        sh.gdense[g] = (!G.listed && p.adj[G.d].fmt == ADJ_DENSE) ? 1 : 0;
         sh.gtpop[g] = __popcll(G.tmask);
         sh.gt_first[g] = G.t_first;
         sh.gt_count[g] = G.t_count;
@@ -2090,15 +2099,19 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
             t->t_state.push_back(q2);
         }
         G.t_count = (int32_t)t->t_unit.size() - G.t_first;
+        // Short rows are listed at discovery where looking them up again
+        // costs several round trips: every adjacency but a dense one (whose
+        // offsets find a row in one; an empty adjacency lists nothing).
+        // Listing costs a reservation per discovery batch, which dense
+        // adjacencies, even mostly empty ones, do not repay.
+        G.listed = g->adj[G.d].fmt != ADJ_DENSE;
         t->groups.push_back(G);
         // a level holds each (state, vertex) pair at most once, so the long
-        // rows of one group are at most the long rows of its adjacency
+        // (listed short) rows of one group are at most the long (short) rows
+        // of its adjacency
         t->row_need += g->long_rows[G.d] + 1;
         t->chunk_need += g->long_chunks[G.d] + 1;
-        // ... and its listed short rows (hypersparse adjacencies only) at
-        // most the short rows of its adjacency
-        if (g->adj[G.d].fmt == ADJ_HYPER) t->srow_need += g->short_rows[G.d];
-        t->srow_need += 1;
+        t->srow_need += (G.listed ? g->short_rows[G.d] : 0) + 1;
     }
     for (size_t u = 0; u < t->units.size(); u++) {
         QUnit &U = t->units[u];
@@ -2383,7 +2396,7 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
 // ------------------------------------------------------------- autotune --
 namespace rpq {
 rpq_status autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas, const int32_t *sources,
-                    float *alpha_out, int32_t *min_out, void *stream) {
+                    float *alpha_out, int32_t *min_out, int32_t *solo_out, void *stream) {
     static const float kAlphas[] = {0.0f, 1.0f, 2.0f, 4.0f, 8.0f, 16.0f, 64.0f};
     static const int32_t kMins[] = {64, 256, 2048};
     const float keep_a = g->pull_alpha;
@@ -2421,20 +2434,54 @@ rpq_status autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas, const i
     }
     g->pull_alpha = best_a;
     g->pull_min = best_m;
+    // then the one-CTA level threshold, under the chosen direction setting
+    static const int32_t kSolo[] = {-1, 512, 2048, 8192};
+    const int32_t keep_s = g->solo_mass, keep_i = g->solo_items;
+    double best_solo = -1;
+    int32_t best_s = keep_s, best_i = keep_i;
+    for (int32_t sm : kSolo) {
+        g->solo_mass = sm;
+        g->solo_items = sm < 0 ? 0 : sm / 8;
+        double total = 0;
+        for (int rep = 0; rep < 2; rep++) {
+            total = 0;
+            for (int32_t i = 0; i < n; i++) {
+                rpq_stats st{};
+                int64_t cnt = 0;
+                rpq_status s = run_query(g, nfas[i]->a, sources[i], 0, nullptr, 0, nullptr,
+                                         nullptr, &st, &cnt, stream);
+                if (s != RPQ_OK) {
+                    g->solo_mass = keep_s;
+                    g->solo_items = keep_i;
+                    return s;
+                }
+                total += st.device_ms;
+            }
+        }
+        if (best_solo < 0 || total < best_solo) {
+            best_solo = total;
+            best_s = g->solo_mass;
+            best_i = g->solo_items;
+        }
+    }
+    g->solo_mass = best_s;
+    g->solo_items = best_i;
     if (alpha_out) *alpha_out = best_a;
     if (min_out) *min_out = best_m;
+    if (solo_out) *solo_out = best_s;
     return RPQ_OK;
 }
 }  // namespace rpq
 
 extern "C" rpq_status rpq_graph_autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
                                          const int32_t *sources, float *alpha_out,
-                                         int32_t *min_pull_out, void *stream) {
+                                         int32_t *min_pull_out, int32_t *solo_mass_out,
+                                         void *stream) {
     rpq::clear_error();
     if (!g || n <= 0 || !nfas || !sources) return rpq::fail(RPQ_ERR_INVALID, "bad argument");
     for (int32_t i = 0; i < n; i++)
         if (!nfas[i]) return rpq::fail(RPQ_ERR_INVALID, "automaton %d is null", i);
-    return rpq::autotune(g, n, nfas, sources, alpha_out, min_pull_out, stream);
+    return rpq::autotune(g, n, nfas, sources, alpha_out, min_pull_out, solo_mass_out, stream);
 }
 
 // --------------------------------------------------- no-allocation entry --

@@ -95,7 +95,7 @@ def lib():
             "rpq_graph_load": [i32, i32, i64, p, p, p, p, pp],
             "rpq_graph_info": [p, i32, p, p, p],
             "rpq_graph_export": [p, i32, i32, p, p, i64],
-            "rpq_graph_autotune": [p, i32, p, p, p, p, p],
+            "rpq_graph_autotune": [p, i32, p, p, p, p, p, p],
             "rpq_nfa_compile": [ctypes.c_char_p, i32, pp],
             "rpq_nfa_from_transitions": [i32, i32, i32, p, p, p, i32, p, i32, p, pp],
             "rpq_nfa_info": [p, p, p, p],
@@ -254,15 +254,16 @@ def rpq_graph_export(g: Graph, label: int, inverse: bool):
 
 
 def rpq_graph_autotune(g: Graph, nfas, sources, stream=None):
-    """Measures the push/pull threshold on sample queries and stores it in the
-    graph; returns (alpha, min_pull)."""
+    """Measures the push/pull threshold and the one-CTA level size on sample
+    queries and stores them in the graph; returns (alpha, min_pull,
+    solo_mass)."""
     n = len(nfas)
     handles = (ctypes.c_void_p * n)(*[x.h.value for x in nfas])
     src, psrc = _host_i32(sources)
-    a, m = ctypes.c_float(), ctypes.c_int32()
+    a, m, so = ctypes.c_float(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().rpq_graph_autotune(g.h, n, handles, psrc, ctypes.byref(a), ctypes.byref(m),
-                                    _stream_handle(stream)))
-    return a.value, m.value
+                                    ctypes.byref(so), _stream_handle(stream)))
+    return a.value, m.value, so.value
 
 
 # ------------------------------------------------------------- automaton --

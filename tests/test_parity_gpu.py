@@ -297,8 +297,9 @@ def test_autotune_keeps_answers():
     texts = ["0*", "1/0*", "(0|1)*/2", "^0/1*"]
     srcs = W.below(92, 1, 8, g.n).tolist()
     nfas = [R.rpq_nfa_compile(texts[i % 4], 4) for i in range(8)]
-    alpha, mn = R.rpq_graph_autotune(gg, nfas, srcs)
+    alpha, mn, solo = R.rpq_graph_autotune(gg, nfas, srcs)
     assert alpha in (0.0, 1.0, 2.0, 4.0, 8.0, 16.0, 64.0) and mn in (64, 256, 2048)
+    assert solo in (-1, 512, 2048, 8192)
     for i in range(8):
         exp = og.ssr(oracle_compile(texts[i % 4], 4), srcs[i])["answer"]
         assert R.rpq_query(gg, nfas[i], srcs[i]).tolist() == exp.tolist()
