@@ -309,7 +309,8 @@ __global__ void long_rows_kernel(DevAdj A, int32_t minlen, int32_t chunk,
         const int32_t deg = A.off[r + 1] - A.off[r];
         if (deg >= minlen) {
             nr++;
-            nc += (unsigned long long)((deg + chunk - 1) / chunk);
+            // chunks start on 16-byte boundaries: up to 3 ids before the row
+            nc += (unsigned long long)((deg + 3 + chunk - 1) / chunk);
         } else if (deg > 0) {
             ns++;
         }
@@ -578,7 +579,8 @@ extern "C" rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64
         }
         // compacted triples: label -> o[1], major -> o[2], minor -> owned neighbour buffer
         DevBuf *nb = side == 0 ? &g->csr_nbr : &g->csc_nbr;
-        if (!nb->alloc(sizeof(int32_t) * std::max<int64_t>(mu, 1)))
+        // 4 ids of padding: a 16-byte load of the last ids never leaves the buffer
+        if (!nb->alloc(sizeof(int32_t) * (std::max<int64_t>(mu, 1) + 4)))
             return fail(RPQ_ERR_OOM, "neighbour array");
         if (m > 0) {
             compact_kernel<<<grid_for(m), 256, 0, st>>>(r[0], r[1], r[2], m, o[0],

@@ -436,6 +436,13 @@ struct LevelCtx {
     // p.srl[slot] (read from the parameters when used, not held in registers)
 };
 
+// Ids of a row before the 16-byte boundary at or below its start: chunks of
+// a long row begin on such boundaries so that every lane loads its 4 ids
+// with one 128-bit load.
+__device__ __forceinline__ int32_t row_skew(const int32_t *nbr, int32_t rb) {
+    return (int32_t)(((uintptr_t)(nbr + rb) >> 2) & 3);
+}
+
 // Lanes with `found` have discovered the new pair (q2, w) of the next level.
 // Appends it to the visited list of q2, sets its frontier bit, and measures
 // its rows for every group leaving q2 (gsf[q2] .. gsf[q2+1]).  q2 must be
@@ -486,7 +493,7 @@ __device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t 
         const bool lng = found && deg >= kWarpRow;
         const unsigned ml = __ballot_sync(kFull, lng);
         if (!ml) continue;
-        const int nch = lng ? (deg + kChunk - 1) / kChunk : 0;
+        const int nch = lng ? (deg + row_skew(sh.gnbr[g], rb) + kChunk - 1) / kChunk : 0;
         int incl = nch;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -569,7 +576,9 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
                 acc_b += 8ull + 4ull * (unsigned long long)deg;
                 acc_e += (unsigned long long)deg * (unsigned long long)sh.gtpop[g];
             }
-            nch[r] = (found[r] && deg >= kWarpRow) ? (deg + kChunk - 1) / kChunk : 0;
+            nch[r] = (found[r] && deg >= kWarpRow)
+                         ? (deg + row_skew(sh.gnbr[g], rb[r]) + kChunk - 1) / kChunk
+                         : 0;
             my_rows += nch[r] ? 1 : 0;
             my_chunks += nch[r];
             my_short += (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) ? 1 : 0;
@@ -797,17 +806,24 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
             const uint64_t tmv = sh.tpush[g];
             if (!tmv) continue;  // warp-uniform
             const int32_t rb = be.x, re = be.y;
-            const int32_t b = rb + (int32_t)((c - c0r) * kChunk);
-            const int32_t e = min(re, b + kChunk);
             const int32_t *nbr = sh.gnbr[g];
+            // the chunk's 128 ids from a 16-byte boundary: lane i loads ids
+            // 4i..4i+3 with one 128-bit load; ids outside the row are masked
+            const int32_t b = rb - row_skew(nbr, rb) + (int32_t)((c - c0r) * kChunk);
+            const int32_t e = min(re, b + kChunk);
+            const int32_t k0 = b + 4 * (int32_t)lane;
+            int4 v4 = make_int4(0, 0, 0, 0);
+            if (k0 < e) v4 = __ldg(reinterpret_cast<const int4 *>(nbr + k0));
+            const int32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+            static_assert(kR == 4, "one 128-bit load per lane and round");
             bool valid[kR];
             uint64_t tm[kR];
             int32_t w[kR];
 #pragma unroll
             for (int r = 0; r < kR; r++) {
-                const int32_t k = b + r * 32 + (int32_t)lane;
-                valid[r] = k < e;
-                w[r] = valid[r] ? __ldg(nbr + k) : 0;
+                const int32_t k = k0 + r;
+                valid[r] = k >= rb && k < e;
+                w[r] = valid[r] ? vv[r] : 0;
                 tm[r] = tmv;
             }
             relax_batch(p, sh, gsf, L, valid, tm, w);
