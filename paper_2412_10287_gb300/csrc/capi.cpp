@@ -6,7 +6,9 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 
 #include "rpq_internal.h"
@@ -87,13 +89,36 @@ extern "C" rpq_status rpq_set_allocator(void *(*alloc)(size_t, void *), void (*f
 
 // ------------------------------------------------------------ automata --
 
+namespace {
+// Compiled automata of recent expressions, by (text, label count): a query
+// stream repeats its templates, and a copy of a small automaton is far
+// cheaper than Glushkov + subset construction + minimisation again.
+std::mutex g_compiled_mu;
+std::map<std::pair<std::string, int32_t>, Automaton> g_compiled;
+constexpr size_t kCompiledMax = 4096;
+}  // namespace
+
 extern "C" rpq_status rpq_nfa_compile(const char *regex, int32_t n_labels, rpq_nfa **out) {
     clear_error();
     if (!out) return fail(RPQ_ERR_INVALID, "out is null");
     *out = nullptr;
     std::unique_ptr<rpq_nfa> h(new rpq_nfa());
+    if (regex) {
+        std::lock_guard<std::mutex> lk(g_compiled_mu);
+        auto it = g_compiled.find({std::string(regex), n_labels});
+        if (it != g_compiled.end()) {
+            h->a = it->second;
+            *out = h.release();
+            return RPQ_OK;
+        }
+    }
     rpq_status s = compile_regex(regex, n_labels, &h->a);
     if (s != RPQ_OK) return s;
+    {
+        std::lock_guard<std::mutex> lk(g_compiled_mu);
+        if (g_compiled.size() >= kCompiledMax) g_compiled.clear();
+        g_compiled.emplace(std::make_pair(std::string(regex), n_labels), h->a);
+    }
     *out = h.release();
     return RPQ_OK;
 }
