@@ -431,7 +431,6 @@ struct LevelCtx {
     int32_t *VL;
     const long long *vnext;       // first list entry of the level being discovered
     uint64_t *F;                  // frontier bits of that level, or null (not kept)
-    unsigned long long *s_acc;    // [2] per-CTA push bytes / product edges
     // its long-row list, chunk map and short-row list are p.rows / p.cmap /
     // p.srl[slot] (read from the parameters when used, not held in registers)
 };
@@ -443,94 +442,15 @@ __device__ __forceinline__ int32_t row_skew(const int32_t *nbr, int32_t rb) {
     return (int32_t)(((uintptr_t)(nbr + rb) >> 2) & 3);
 }
 
-// Lanes with `found` have discovered the new pair (q2, w) of the next level.
-// Appends it to the visited list of q2, sets its frontier bit, and measures
-// its rows for every group leaving q2 (gsf[q2] .. gsf[q2+1]).  q2 must be
-// warp-uniform; all 32 lanes must call.
-__device__ void warp_discover(const KParams &p, const Shared &sh, const int32_t *gsf,
-                              const LevelCtx &L, bool found, int q2, int32_t w) {
-    const unsigned m = __ballot_sync(kFull, found);
-    if (!m) return;
-    const unsigned lane = lane_id();
-    const int leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if ((int)lane == leader)
-        base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)__popc(m));
-    base = __shfl_sync(kFull, base, leader);
-    if (found) {
-        L.VL[(size_t)q2 * p.n + L.vnext[q2] + base + __popc(m & lanemask_lt())] = w;
-        if (L.F)
-            atomicOr((unsigned long long *)(L.F + (size_t)q2 * p.W + ((uint32_t)w >> 6)),
-                     1ull << (w & 63));
-    }
-    unsigned long long acc_b = 0, acc_e = 0;
-    for (int g = gsf[q2]; g < gsf[q2 + 1]; g++) {
-        int32_t rb = 0, re = 0;
-        if (found) adj_row(p.adj[sh.gd[g]], w, rb, re);
-        const int32_t deg = re - rb;
-        if (found) {
-            if (deg) atomicAdd(&sh.s_mf[g], (unsigned long long)deg);
-            acc_b += 8ull + 4ull * (unsigned long long)deg;
-            acc_e += (unsigned long long)deg * (unsigned long long)sh.gtpop[g];
-        }
-        // short rows of a hypersparse adjacency: warp-aggregated append to the
-        // level's short-row list (dense ones are found again from the
-        // frontier list and the offsets, one round trip)
-        const bool sht = found && deg > 0 && deg < kWarpRow && !sh.gdense[g];
-        const unsigned msh = __ballot_sync(kFull, sht);
-        if (msh) {
-            const int ls = __ffs(msh) - 1;
-            unsigned long long sb = 0;
-            if ((int)lane == ls) sb = atomicAdd(&L.C->srows[L.slot], (unsigned long long)__popc(msh));
-            sb = __shfl_sync(kFull, sb, ls);
-            if (sht) {
-                const long long at = (long long)sb + __popc(msh & lanemask_lt());
-                if (at < p.srow_cap) p.srl[L.slot][at] = make_int4(g, rb, re, w);
-                else atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
-            }
-        }
-        // long rows: warp-aggregated append to the chunk list
-        const bool lng = found && deg >= kWarpRow;
-        const unsigned ml = __ballot_sync(kFull, lng);
-        if (!ml) continue;
-        const int nch = lng ? (deg + row_skew(sh.gnbr[g], rb) + kChunk - 1) / kChunk : 0;
-        int incl = nch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if ((int)lane >= o) incl += y;
-        }
-        const int tot = __shfl_sync(kFull, incl, 31);
-        const int ld = __ffs(ml) - 1;
-        unsigned long long old = 0;
-        if ((int)lane == ld)
-            old = atomicAdd(&L.C->rows[L.slot],
-                            ((unsigned long long)__popc(ml) << 40) | (unsigned long long)tot);
-        old = __shfl_sync(kFull, old, ld);
-        if (lng) {
-            const long long ri = (long long)(old >> 40) + __popc(ml & lanemask_lt());
-            const long long cb = (long long)(old & ((1ull << 40) - 1)) + (incl - nch);
-            if (ri < p.row_cap && cb + nch <= p.chunk_cap) {
-                p.rows[L.slot][ri] = Row{g, w, rb, re, cb};
-                for (int k = 0; k < nch; k++) p.cmap[L.slot][cb + k] = (int32_t)ri;
-            } else {
-                atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
-            }
-        }
-    }
-    if (acc_b) atomicAdd(&L.s_acc[0], acc_b);
-    if (acc_e) atomicAdd(&L.s_acc[1], acc_e);
-}
-
-// Batched discovery: lanes with found[r] have discovered (q2, w[r]).  Same
-// effect as kR calls of warp_discover, with the round trips of the kR
-// entries overlapped: one list reservation, one set of row-length loads per
-// group, one chunk-list reservation per group.  q2 warp-uniform; all 32
-// lanes must call.
+// Lanes with found[r] have discovered the new pair (q2, w[r]) of the next
+// level: appended to the visited list of q2 (one reservation for the warp)
+// and, on grid levels, its frontier bit set.  The rows the pair will expand
+// are measured after the level (measure_level), with many lookups in flight
+// instead of one chain per discovery.  q2 warp-uniform; all 32 lanes call.
 template <int kB>
-__device__ void warp_discover_batch(const KParams &p, const Shared &sh, const int32_t *gsf,
-                                    const LevelCtx &L, const bool (&found)[kB], int q2,
-                                    const int32_t (&w)[kB]) {
+__device__ __forceinline__ void warp_discover_batch(const KParams &p, const LevelCtx &L,
+                                                    const bool (&found)[kB], int q2,
+                                                    const int32_t (&w)[kB]) {
     unsigned m[kB];
     int total = 0;
 #pragma unroll
@@ -540,7 +460,6 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
     }
     if (!total) return;
     const unsigned lane = lane_id();
-    const int g_first = gsf[q2], g_end = gsf[q2 + 1];
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)total);
     base = __shfl_sync(kFull, base, 0);
@@ -556,8 +475,27 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
         }
         run += __popc(m[r]);
     }
-    unsigned long long acc_b = 0, acc_e = 0;
-    for (int g = g_first; g < g_end; g++) {
+}
+
+__device__ __forceinline__ void warp_discover(const KParams &p, const LevelCtx &L, bool found,
+                                              int q2, int32_t w) {
+    const bool f[1] = {found};
+    const int32_t x[1] = {w};
+    warp_discover_batch<1>(p, L, f, q2, x);
+}
+
+// Rows of new pairs (q, w[r]) of the level in counter slot `slot`, for every
+// group leaving q: edge mass per group (the next push/pull choice), rows of
+// >= kWarpRow edges to the long-row list (128-edge chunks from a 16-byte
+// boundary), short rows of listed groups to the short-row list, and the push
+// bytes / product edges of the rows.  q warp-uniform; all 32 lanes call.
+template <int kB>
+__device__ __forceinline__ void measure_rows(const KParams &p, const Shared &sh, const int32_t *gsf,
+                                             const Ctrs &C, int slot, const bool (&found)[kB],
+                                             int q, const int32_t (&w)[kB],
+                                             unsigned long long &acc_b, unsigned long long &acc_e) {
+    const unsigned lane = lane_id();
+    for (int g = gsf[q]; g < gsf[q + 1]; g++) {
         const DevAdj A = p.adj[sh.gd[g]];
         int32_t rb[kB], re[kB];
 #pragma unroll
@@ -600,10 +538,9 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
         const int ts = tpk & 0xffff, tr = tpk >> 16;
         if (!ts && !tr) continue;  // warp-uniform
         unsigned long long sb = 0, old = 0;
-        if (lane == 31 && ts) sb = atomicAdd(&L.C->srows[L.slot], (unsigned long long)ts);
+        if (lane == 31 && ts) sb = atomicAdd(&C.srows[slot], (unsigned long long)ts);
         if (lane == 0 && tr)
-            old = atomicAdd(&L.C->rows[L.slot],
-                            ((unsigned long long)tr << 40) | (unsigned long long)tc);
+            old = atomicAdd(&C.rows[slot], ((unsigned long long)tr << 40) | (unsigned long long)tc);
         sb = __shfl_sync(kFull, sb, 31);
         old = __shfl_sync(kFull, old, 0);
         if (ts) {
@@ -612,7 +549,7 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
             for (int r = 0; r < kB; r++) {
                 const int32_t deg = re[r] - rb[r];
                 if (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) {
-                    if (at < p.srow_cap) p.srl[L.slot][at] = make_int4(g, rb[r], re[r], w[r]);
+                    if (at < p.srow_cap) p.srl[slot][at] = make_int4(g, rb[r], re[r], w[r]);
                     else atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
                     at++;
                 }
@@ -626,8 +563,8 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
         for (int r = 0; r < kB; r++) {
             if (!nch[r]) continue;
             if (ri < p.row_cap && cb + nch[r] <= p.chunk_cap) {
-                p.rows[L.slot][ri] = Row{g, w[r], rb[r], re[r], cb};
-                for (int k = 0; k < nch[r]; k++) p.cmap[L.slot][cb + k] = (int32_t)ri;
+                p.rows[slot][ri] = Row{g, w[r], rb[r], re[r], cb};
+                for (int k = 0; k < nch[r]; k++) p.cmap[slot][cb + k] = (int32_t)ri;
             } else {
                 atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
             }
@@ -635,8 +572,61 @@ __device__ void warp_discover_batch(const KParams &p, const Shared &sh, const in
             cb += nch[r];
         }
     }
-    if (acc_b) atomicAdd(&L.s_acc[0], acc_b);
-    if (acc_e) atomicAdd(&L.s_acc[1], acc_e);
+}
+
+// After level j: measures the rows of every pair it discovered (level j+1's
+// frontier: VL[q][vnext[q], vnext[q] + n_q), n_q in counter slot `slot` of
+// C), on CTA `cta` of `ncta`, kR pairs per lane with their lookups in flight
+// together; then this CTA's sums of edge mass and push bytes / product edges
+// go to the slot's counters.
+__device__ void measure_level(const KParams &p, const Shared &sh, const int32_t *gsf, const Ctrs &C,
+                              int slot, int cta, int ncta, unsigned long long *s_acc) {
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    __shared__ long long s_cnt[kMaxStates];  // new pairs per state, read in one round trip
+    if (threadIdx.x < p.S)
+        s_cnt[threadIdx.x] = (long long)*(volatile unsigned long long *)&C.fl[slot * kMaxStates + threadIdx.x];
+    __syncthreads();
+    unsigned long long acc_b = 0, acc_e = 0;
+    const long long wstride = (long long)ncta * kWarps * 32 * kR;
+    for (int q = 0; q < p.S; q++) {
+        if (gsf[q] == gsf[q + 1]) continue;  // no group leaves q
+        const long long cnt = s_cnt[q];
+        const int32_t *lst = p.VL + (size_t)q * p.n + sh.vnext[q];
+        for (long long b0 = ((long long)cta * kWarps + warp) * 32 * kR; b0 < cnt; b0 += wstride) {
+            bool ok[kR];
+            int32_t w[kR];
+#pragma unroll
+            for (int r = 0; r < kR; r++) {
+                const long long i = b0 + r * 32 + lane;
+                ok[r] = i < cnt;
+                w[r] = ok[r] ? __ldcg(lst + i) : 0;
+            }
+            measure_rows<kR>(p, sh, gsf, C, slot, ok, q, w, acc_b, acc_e);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_b += __shfl_down_sync(kFull, acc_b, o);
+        acc_e += __shfl_down_sync(kFull, acc_e, o);
+    }
+    if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
+    __syncthreads();
+    if (lane == 0) {
+        if (acc_b) atomicAdd(&s_acc[0], acc_b);
+        if (acc_e) atomicAdd(&s_acc[1], acc_e);
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
+        const unsigned long long v = sh.s_mf[g];
+        if (v) {
+            atomicAdd(&C.mf[slot * C.mstride + g], v);
+            sh.s_mf[g] = 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (s_acc[0]) atomicAdd(&C.bytes[slot], s_acc[0]);
+        if (s_acc[1]) atomicAdd(&C.edges[slot], s_acc[1]);
+    }
 }
 
 // General relaxation (any number of target states per lane): edge (., w)
@@ -660,7 +650,7 @@ __device__ void relax_general(const KParams &p, const Shared &sh, const int32_t 
                 found = !(old & bit);
             }
         }
-        warp_discover(p, sh, gsf, L, found, q2, w);
+        warp_discover(p, L, found, q2, w);
     }
 }
 
@@ -702,7 +692,7 @@ __device__ __forceinline__ void relax_batch(const KParams &p, const Shared &sh, 
             act[r] = !(old & bit);
         }
     }
-    warp_discover_batch<kR>(p, sh, gsf, L, act, q2, w);
+    warp_discover_batch<kR>(p, L, act, q2, w);
 }
 
 // ---------------------------------------------------------------- phases -
@@ -751,7 +741,8 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     // go to device memory on a grid level, to CTA 0's shared memory otherwise
     const Ctrs &Cc = sh.cv[cur_smem ? 1 : 0];
     const Ctrs &Cn = sh.cv[on_grid ? 0 : 1];
-    LevelCtx L{ns, &Cn, p.VL, sh.vnext, on_grid ? p.F[ns] : nullptr, s_acc};
+    (void)s_acc;
+    LevelCtx L{ns, &Cn, p.VL, sh.vnext, on_grid ? p.F[ns] : nullptr};
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
@@ -1057,21 +1048,10 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
                 disc[h] = !(old & bit);
             }
         }
-        warp_discover_batch<kPullRows>(p, sh, gsf, L, disc, uq2, w);
+        warp_discover_batch<kPullRows>(p, L, disc, uq2, w);
     }
 
-    // per-CTA sums of this level's discoveries
-    __syncthreads();
-    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
-        const unsigned long long v = sh.s_mf[g];
-        if (v) {
-            atomicAdd(&Cn.mf[ns * Cn.mstride + g], v);
-            sh.s_mf[g] = 0;
-        }
-    }
     if (threadIdx.x == 0) {
-        if (s_acc[0]) atomicAdd(&Cn.bytes[ns], s_acc[0]);
-        if (s_acc[1]) atomicAdd(&Cn.edges[ns], s_acc[1]);
         if (p.trace && j < p.trace_cap) {  // spread of the CTAs' finishing times
             const unsigned long long t = global_timer_ns();
             atomicMax(&p.trace[(size_t)j * kTraceFields + 10], ~t);
@@ -1767,7 +1747,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         }
         if (threadIdx.x < 32) {
             // like every solo level, no frontier bits
-            LevelCtx L0{0, &sh.cv[1], p.VL, sh.vnext, nullptr, s_acc};
+            LevelCtx L0{0, &sh.cv[1], p.VL, sh.vnext, nullptr};
             const uint32_t swi = (uint32_t)p.source >> 6;
             const uint64_t sbit = 1ull << (p.source & 63);
             uint64_t sm = p.start_mask;
@@ -1776,19 +1756,11 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
                 sm &= sm - 1;
                 if (lane_id() == 0)
                     atomicOr((unsigned long long *)(p.P + (size_t)q * p.W + swi), sbit);
-                warp_discover(p, sh, s_gsf, L0, lane_id() == 0, q, p.source);
-            }
-            __syncwarp();
-            if (threadIdx.x == 0) {
-                sh.cv[1].bytes[0] = s_acc[0];
-                sh.cv[1].edges[0] = s_acc[1];
-                s_acc[0] = s_acc[1] = 0;
-            }
-            for (int g = threadIdx.x; g < p.n_groups; g += 32) {
-                sh.cv[1].mf[g] = sh.s_mf[g];
-                sh.s_mf[g] = 0;
+                warp_discover(p, L0, lane_id() == 0, q, p.source);
             }
         }
+        __syncthreads();
+        measure_level(p, sh, s_gsf, sh.cv[1], 0, 0, 1, s_acc);
         __syncthreads();
         if (p.trace && threadIdx.x == 0)
             p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
@@ -1860,9 +1832,15 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         prev_grid = grid;
         cur_smem = !grid;
         trace_put(p, j, 1, global_timer_ns());
+        // level j+1 is complete: measure the rows of its pairs, then plan it
         if (grid) {
             if (!grid_barrier(p.c)) return;
+            measure_level(p, sh, s_gsf, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
+                          s_acc);
+            if (!grid_barrier(p.c)) return;
         } else {
+            __syncthreads();
+            measure_level(p, sh, s_gsf, sh.cv[1], (j + 1) % 3, 0, 1, s_acc);
             __syncthreads();
             heartbeat(p);
             if (load_status(p.c) != 0) return;
