@@ -798,21 +798,29 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
             if (!tmv) continue;  // warp-uniform
             const int32_t rb = be.x, re = be.y;
             const int32_t *nbr = sh.gnbr[g];
-            // the chunk's 128 ids from a 16-byte boundary: lane i loads ids
-            // 4i..4i+3 with one 128-bit load; ids outside the row are masked
+            // the chunk's kChunk ids from a 16-byte boundary: lane i loads
+            // its kR ids with kR / 4 128-bit loads (ids 4i.. of each 128-id
+            // block); ids outside the row are masked
             const int32_t b = rb - row_skew(nbr, rb) + (int32_t)((c - c0r) * kChunk);
             const int32_t e = min(re, b + kChunk);
-            const int32_t k0 = b + 4 * (int32_t)lane;
-            int4 v4 = make_int4(0, 0, 0, 0);
-            if (k0 < e) v4 = __ldg(reinterpret_cast<const int4 *>(nbr + k0));
-            const int32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
-            static_assert(kR == 4, "one 128-bit load per lane and round");
+            static_assert(kR % 4 == 0, "whole 128-bit loads per lane and round");
+            int32_t vv[kR];
+#pragma unroll
+            for (int h = 0; h < kR / 4; h++) {
+                const int32_t k0 = b + h * 128 + 4 * (int32_t)lane;
+                int4 v4 = make_int4(0, 0, 0, 0);
+                if (k0 < e) v4 = __ldg(reinterpret_cast<const int4 *>(nbr + k0));
+                vv[4 * h] = v4.x;
+                vv[4 * h + 1] = v4.y;
+                vv[4 * h + 2] = v4.z;
+                vv[4 * h + 3] = v4.w;
+            }
             bool valid[kR];
             uint64_t tm[kR];
             int32_t w[kR];
 #pragma unroll
             for (int r = 0; r < kR; r++) {
-                const int32_t k = k0 + r;
+                const int32_t k = b + (r / 4) * 128 + 4 * (int32_t)lane + (r & 3);
                 valid[r] = k >= rb && k < e;
                 w[r] = valid[r] ? vv[r] : 0;
                 tm[r] = tmv;
