@@ -441,18 +441,6 @@ __global__ void lane_write_kernel(const uint32_t *__restrict__ A32, int64_t word
     }
 }
 
-__global__ void lane_seed_kernel(const int32_t *__restrict__ seeds, int n_seeds, int32_t K,
-                                 uint64_t *__restrict__ M, uint64_t *__restrict__ P) {
-    // seeds: (v, k, lw, mask_lo, mask_hi) records of 5 int32
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_seeds; i += gridDim.x * blockDim.x) {
-        const int32_t *s = seeds + 5 * i;
-        const uint64_t m = (uint64_t)(uint32_t)s[3] | ((uint64_t)(uint32_t)s[4] << 32);
-        const size_t idx = ((size_t)s[0] * K + s[1]) * kLW + s[2];
-        atomicOr((unsigned long long *)(M + idx), (unsigned long long)m);
-        atomicOr((unsigned long long *)(P + idx), (unsigned long long)m);
-    }
-}
-
 // ---- one level step as separate kernels (server: captured in a graph) ----
 __global__ void __launch_bounds__(kLThreads) lane_step_vertices_kernel(LParams p) {
     extern __shared__ __align__(16) uint64_t lsm[];
