@@ -399,7 +399,9 @@ def rpq_query_batch(g: Graph, nfas, sources, max_levels: int = 0, stream=None,
     src, psrc = _host_i32(sources)
     offs = np.zeros(n + 1, np.int64)
     stats = (RpqStats * max(n, 1))() if with_stats else None
-    cap = 1 << 20
+    # room for every answer up to 2^27 ids (pages are only touched as written),
+    # so that a second traversal for a larger buffer is rarely needed
+    cap = max(1, min(n * g.n, 1 << 27))
     while True:
         buf = np.empty(max(cap, 1), np.int32)
         s = _check(lib().rpq_query_batch(g.h, n, handles, psrc, int(max_levels), _ptr(offs),
