@@ -381,3 +381,45 @@ def test_last_answer_two_call_pattern():
     R.rpq_query(gg, nfa, srcs[0], out=out)
     ptr, n = ctypes.POINTER(ctypes.c_int32)(), ctypes.c_int64()
     assert R.lib().rpq_last_answer(ctypes.byref(ptr), ctypes.byref(n)) == R.RPQ_ERR_INVALID
+
+
+def test_concurrent_host_threads_share_a_graph():
+    """Graphs and automata are shared by host threads: eight threads query
+    one graph at once (each call takes its own workspace and stream; host
+    answers go through each thread's own pinned buffer)."""
+    import threading
+
+    import torch
+
+    g = W.rmat_graph(13, 80000, 4, seed=95)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    texts = ["0*", "1/(0|2)*", "(0|^1)*/2", "^3/1*", "(0/1)*"]
+    nfas = [R.rpq_nfa_compile(t, 4) for t in texts]
+    srcs = W.below(96, 1, 64, g.n).tolist()
+    exp = {(i % 5, s): og.ssr(oracle_compile(texts[i % 5], 4), s)["answer"].tolist()
+           for i, s in enumerate(srcs)}
+    errors = []
+
+    def worker(tid):
+        try:
+            stream = torch.cuda.Stream()
+            for k in range(tid, len(srcs), 8):
+                key = (k % 5, srcs[k])
+                got = R.rpq_query(gg, nfas[k % 5], srcs[k], stream=stream)
+                if got.tolist() != exp[key]:
+                    errors.append(("host", key))
+                out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                c = R.rpq_query(gg, nfas[k % 5], srcs[k], out=out, stream=stream)
+                stream.synchronize()
+                if out[:c].cpu().tolist() != exp[key]:
+                    errors.append(("device", key))
+        except Exception as e:  # reported below
+            errors.append(("raised", repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors[:5]
