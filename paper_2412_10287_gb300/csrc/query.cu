@@ -92,8 +92,12 @@ struct Row {
 // Device counters of one query.  Per-level fields rotate over 3 slots:
 // slot j % 3 holds level j.
 struct Counters {
-    unsigned bar_count, bar_gen;
-    int32_t status, pub_level;
+    unsigned bar_count;
+    int32_t pub_level;
+    // (grid barrier generation << 32) | status (0, or the rpq_status that
+    // stopped the query): the load that ends a CTA's barrier wait also tells
+    // it whether the query failed
+    unsigned long long gen_status;
     unsigned long long gate;  // (launch epoch << 32) | releases of the gate so far
     unsigned long long beat;  // CTA 0's progress while it runs levels alone
     unsigned long long parked;  // CTAs that have parked (cumulative over the launch)
@@ -194,38 +198,57 @@ __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsign
 }
 
 // ------------------------------------------------------------ barrier ----
+__host__ __device__ __forceinline__ int32_t status_of(unsigned long long gen_status) {
+    return (int32_t)(uint32_t)gen_status;
+}
+
 __device__ __forceinline__ int load_status(const Counters *c) {
-    return *(volatile const int32_t *)&c->status;
+    return status_of(*(volatile const unsigned long long *)&c->gen_status);
+}
+
+// Records the first failure of the query (later ones are dropped).
+__device__ __forceinline__ void set_status(Counters *c, int32_t err) {
+    unsigned long long old = *(volatile unsigned long long *)&c->gen_status;
+    while (status_of(old) == 0) {
+        const unsigned long long seen =
+            atomicCAS(&c->gen_status, old, (old & ~0xffffffffull) | (uint32_t)err);
+        if (seen == old) break;
+        old = seen;  // a barrier moved the generation on: try again
+    }
 }
 
 __device__ __forceinline__ bool grid_barrier(Counters *c) {
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *genp = &c->bar_gen;
-        const unsigned gen = *genp;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        // arrive with release semantics (this CTA's writes, ordered by the
+        // __syncthreads above), leave with acquire semantics
+        unsigned long long w = *(volatile unsigned long long *)&c->gen_status;
+        const unsigned gen = (unsigned)(w >> 32);
+        unsigned arrived;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&c->bar_count) : "memory");
         if (arrived == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
+            asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(&c->bar_count) : "memory");
+            asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], %2;"
+                         : "=l"(w)
+                         : "l"(&c->gen_status), "l"(1ull << 32)
+                         : "memory");
         } else {
             const uint64_t t0 = global_timer_ns();
-            unsigned it = 0;
-            while (*genp == gen) {
-                if ((++it & 255u) == 0) {
-                    if (load_status(c) != 0) break;
-                    if (global_timer_ns() - t0 > kBarrierTimeoutNs) {
-                        atomicCAS(&c->status, 0, (int32_t)RPQ_ERR_TIMEOUT);
-                        break;
-                    }
+            for (unsigned it = 1;; it++) {
+                asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(w) : "l"(&c->gen_status) : "memory");
+                if ((unsigned)(w >> 32) != gen || status_of(w) != 0) break;
+                if ((it & 255u) == 0 && global_timer_ns() - t0 > kBarrierTimeoutNs) {
+                    set_status(c, (int32_t)RPQ_ERR_TIMEOUT);
+                    w = 1;
+                    break;
                 }
             }
         }
-        __threadfence();
+        s_ok = status_of(w) == 0;
     }
     __syncthreads();
-    return load_status(c) == 0;
+    return s_ok != 0;
 }
 
 // ------------------------------------------------------- shared layout ---
@@ -484,126 +507,151 @@ __device__ __forceinline__ void warp_discover(const KParams &p, const LevelCtx &
     warp_discover_batch<1>(p, L, f, q2, x);
 }
 
-// Rows of new pairs (q, w[r]) of the level in counter slot `slot`, for every
-// group leaving q: edge mass per group (the next push/pull choice), rows of
-// >= kWarpRow edges to the long-row list (128-edge chunks from a 16-byte
-// boundary), short rows of listed groups to the short-row list, and the push
-// bytes / product edges of the rows.  q warp-uniform; all 32 lanes call.
+// Rows in group g of new pairs (q, w[r]) of the level in counter slot
+// `slot` (q the group's source state): edge mass of the group (the next
+// push/pull choice), rows of >= kWarpRow edges to the long-row list
+// (128-edge chunks from a 16-byte boundary), short rows of a listed group to
+// the short-row list, and the push bytes / product edges of the rows.
+// g warp-uniform; all 32 lanes call.
 template <int kB>
-__device__ __forceinline__ void measure_rows(const KParams &p, const Shared &sh, const int32_t *gsf,
-                                             const Ctrs &C, int slot, const bool (&found)[kB],
-                                             int q, const int32_t (&w)[kB],
+__device__ __forceinline__ void measure_rows(const KParams &p, const Shared &sh, const Ctrs &C,
+                                             int slot, const bool (&found)[kB], int g,
+                                             const int32_t (&w)[kB],
                                              unsigned long long &acc_b, unsigned long long &acc_e) {
     const unsigned lane = lane_id();
-    for (int g = gsf[q]; g < gsf[q + 1]; g++) {
-        const DevAdj A = p.adj[sh.gd[g]];
-        int32_t rb[kB], re[kB];
+    const DevAdj A = p.adj[sh.gd[g]];
+    int32_t rb[kB], re[kB];
 #pragma unroll
-        for (int r = 0; r < kB; r++) {
-            rb[r] = re[r] = 0;
-            if (found[r]) adj_row(A, w[r], rb[r], re[r]);
+    for (int r = 0; r < kB; r++) {
+        rb[r] = re[r] = 0;
+        if (found[r]) adj_row(A, w[r], rb[r], re[r]);
+    }
+    int nch[kB];
+    int my_rows = 0, my_chunks = 0, my_short = 0;
+    unsigned long long mass = 0;
+#pragma unroll
+    for (int r = 0; r < kB; r++) {
+        const int32_t deg = re[r] - rb[r];
+        if (found[r]) {
+            mass += (unsigned long long)deg;
+            acc_b += 8ull + 4ull * (unsigned long long)deg;
+            acc_e += (unsigned long long)deg * (unsigned long long)sh.gtpop[g];
         }
-        int nch[kB];
-        int my_rows = 0, my_chunks = 0, my_short = 0;
-        unsigned long long mass = 0;
+        nch[r] = (found[r] && deg >= kWarpRow)
+                     ? (deg + row_skew(sh.gnbr[g], rb[r]) + kChunk - 1) / kChunk
+                     : 0;
+        my_rows += nch[r] ? 1 : 0;
+        my_chunks += nch[r];
+        my_short += (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) ? 1 : 0;
+    }
+    if (mass) atomicAdd(&sh.s_mf[g], mass);
+    // warp prefix of (short rows | long rows << 16, chunks); one
+    // reservation in each list, both in flight together
+    int ipk = my_short | (my_rows << 16), ic = my_chunks;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int yp = __shfl_up_sync(kFull, ipk, o);
+        const int yc = __shfl_up_sync(kFull, ic, o);
+        if ((int)lane >= o) {
+            ipk += yp;
+            ic += yc;
+        }
+    }
+    const int tpk = __shfl_sync(kFull, ipk, 31), tc = __shfl_sync(kFull, ic, 31);
+    const int ts = tpk & 0xffff, tr = tpk >> 16;
+    if (!ts && !tr) return;  // warp-uniform
+    unsigned long long sb = 0, old = 0;
+    if (lane == 31 && ts) sb = atomicAdd(&C.srows[slot], (unsigned long long)ts);
+    if (lane == 0 && tr)
+        old = atomicAdd(&C.rows[slot], ((unsigned long long)tr << 40) | (unsigned long long)tc);
+    sb = __shfl_sync(kFull, sb, 31);
+    old = __shfl_sync(kFull, old, 0);
+    if (ts) {
+        long long at = (long long)sb + ((ipk & 0xffff) - my_short);
 #pragma unroll
         for (int r = 0; r < kB; r++) {
             const int32_t deg = re[r] - rb[r];
-            if (found[r]) {
-                mass += (unsigned long long)deg;
-                acc_b += 8ull + 4ull * (unsigned long long)deg;
-                acc_e += (unsigned long long)deg * (unsigned long long)sh.gtpop[g];
+            if (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) {
+                if (at < p.srow_cap) p.srl[slot][at] = make_int4(g, rb[r], re[r], w[r]);
+                else set_status(p.c, (int32_t)RPQ_ERR_OOM);
+                at++;
             }
-            nch[r] = (found[r] && deg >= kWarpRow)
-                         ? (deg + row_skew(sh.gnbr[g], rb[r]) + kChunk - 1) / kChunk
-                         : 0;
-            my_rows += nch[r] ? 1 : 0;
-            my_chunks += nch[r];
-            my_short += (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) ? 1 : 0;
         }
-        if (mass) atomicAdd(&sh.s_mf[g], mass);
-        // warp prefix of (short rows | long rows << 16, chunks); one
-        // reservation in each list, both in flight together
-        int ipk = my_short | (my_rows << 16), ic = my_chunks;
+    }
+    if (!tr) return;  // warp-uniform
+    const int ir = ipk >> 16;
+    long long ri = (long long)(old >> 40) + (ir - my_rows);
+    long long cb = (long long)(old & ((1ull << 40) - 1)) + (ic - my_chunks);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int yp = __shfl_up_sync(kFull, ipk, o);
-            const int yc = __shfl_up_sync(kFull, ic, o);
-            if ((int)lane >= o) {
-                ipk += yp;
-                ic += yc;
-            }
+    for (int r = 0; r < kB; r++) {
+        if (!nch[r]) continue;
+        if (ri < p.row_cap && cb + nch[r] <= p.chunk_cap) {
+            p.rows[slot][ri] = Row{g, w[r], rb[r], re[r], cb};
+            for (int k = 0; k < nch[r]; k++) p.cmap[slot][cb + k] = (int32_t)ri;
+        } else {
+            set_status(p.c, (int32_t)RPQ_ERR_OOM);
         }
-        const int tpk = __shfl_sync(kFull, ipk, 31), tc = __shfl_sync(kFull, ic, 31);
-        const int ts = tpk & 0xffff, tr = tpk >> 16;
-        if (!ts && !tr) continue;  // warp-uniform
-        unsigned long long sb = 0, old = 0;
-        if (lane == 31 && ts) sb = atomicAdd(&C.srows[slot], (unsigned long long)ts);
-        if (lane == 0 && tr)
-            old = atomicAdd(&C.rows[slot], ((unsigned long long)tr << 40) | (unsigned long long)tc);
-        sb = __shfl_sync(kFull, sb, 31);
-        old = __shfl_sync(kFull, old, 0);
-        if (ts) {
-            long long at = (long long)sb + ((ipk & 0xffff) - my_short);
-#pragma unroll
-            for (int r = 0; r < kB; r++) {
-                const int32_t deg = re[r] - rb[r];
-                if (found[r] && deg > 0 && deg < kWarpRow && !sh.gdense[g]) {
-                    if (at < p.srow_cap) p.srl[slot][at] = make_int4(g, rb[r], re[r], w[r]);
-                    else atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
-                    at++;
-                }
-            }
-        }
-        if (!tr) continue;  // warp-uniform
-        const int ir = ipk >> 16;
-        long long ri = (long long)(old >> 40) + (ir - my_rows);
-        long long cb = (long long)(old & ((1ull << 40) - 1)) + (ic - my_chunks);
-#pragma unroll
-        for (int r = 0; r < kB; r++) {
-            if (!nch[r]) continue;
-            if (ri < p.row_cap && cb + nch[r] <= p.chunk_cap) {
-                p.rows[slot][ri] = Row{g, w[r], rb[r], re[r], cb};
-                for (int k = 0; k < nch[r]; k++) p.cmap[slot][cb + k] = (int32_t)ri;
-            } else {
-                atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_OOM);
-            }
-            ri++;
-            cb += nch[r];
-        }
+        ri++;
+        cb += nch[r];
     }
 }
 
 // After level j: measures the rows of every pair it discovered (level j+1's
 // frontier: VL[q][vnext[q], vnext[q] + n_q), n_q in counter slot `slot` of
-// C), on CTA `cta` of `ncta`, kR pairs per lane with their lookups in flight
-// together; then this CTA's sums of edge mass and push bytes / product edges
-// go to the slot's counters.
-__device__ void measure_level(const KParams &p, const Shared &sh, const int32_t *gsf, const Ctrs &C,
-                              int slot, int cta, int ncta, unsigned long long *s_acc) {
+// C), on CTA `cta` of `ncta`.  The work is (group, batch of 32 x kR pairs)
+// units spread over every warp, so the groups leaving one state are measured
+// side by side, each lane with its kR lookups in flight together; then this
+// CTA's sums of edge mass and push bytes / product edges go to the slot's
+// counters.
+__device__ void measure_level(const KParams &p, const Shared &sh, const Ctrs &C, int slot, int cta,
+                              int ncta, unsigned long long *s_acc) {
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     __shared__ long long s_cnt[kMaxStates];  // new pairs per state, read in one round trip
     if (threadIdx.x < p.S)
         s_cnt[threadIdx.x] = (long long)*(volatile unsigned long long *)&C.fl[slot * kMaxStates + threadIdx.x];
     __syncthreads();
-    unsigned long long acc_b = 0, acc_e = 0;
-    const long long wstride = (long long)ncta * kWarps * 32 * kR;
-    for (int q = 0; q < p.S; q++) {
-        if (gsf[q] == gsf[q + 1]) continue;  // no group leaves q
-        const long long cnt = s_cnt[q];
-        const int32_t *lst = p.VL + (size_t)q * p.n + sh.vnext[q];
-        for (long long b0 = ((long long)cta * kWarps + warp) * 32 * kR; b0 < cnt; b0 += wstride) {
-            bool ok[kR];
-            int32_t w[kR];
+    // bpre[g] = batches of the groups before g (kept in the gather buffer,
+    // idle between expansions); batch b goes to warp b / ncta of CTA b % ncta
+    static_assert(kMaxGroups < kGather, "batch prefix fits the gather buffer");
+    int32_t *bpre = sh.gbuf_k;
+    if (warp == 0) {
+        int32_t run = 0;
+        for (int g0 = 0; g0 < p.n_groups; g0 += 32) {
+            const int g = g0 + (int)lane;
+            int32_t v = g < p.n_groups ? (int32_t)((s_cnt[sh.gq[g]] + 32 * kR - 1) / (32 * kR)) : 0;
 #pragma unroll
-            for (int r = 0; r < kR; r++) {
-                const long long i = b0 + r * 32 + lane;
-                ok[r] = i < cnt;
-                w[r] = ok[r] ? __ldcg(lst + i) : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, v, o);
+                if ((int)lane >= o) v += y;
             }
-            measure_rows<kR>(p, sh, gsf, C, slot, ok, q, w, acc_b, acc_e);
+            if (g < p.n_groups) bpre[g + 1] = run + v;
+            run += __shfl_sync(kFull, v, 31);
         }
+        if (lane == 0) bpre[0] = 0;
+    }
+    __syncthreads();
+    unsigned long long acc_b = 0, acc_e = 0;
+    const int32_t nbatch = bpre[p.n_groups];
+    for (int32_t b = warp * ncta + cta; b < nbatch; b += ncta * kWarps) {
+        int lo = 0, hi = p.n_groups;  // the last group whose batches start at or before b
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (bpre[mid] <= b) lo = mid; else hi = mid;
+        }
+        const int g = lo, q = sh.gq[g];
+        const long long cnt = s_cnt[q];
+        const long long b0 = (long long)(b - bpre[g]) * 32 * kR;
+        const int32_t *lst = p.VL + (size_t)q * p.n + sh.vnext[q];
+        bool ok[kR];
+        int32_t w[kR];
+#pragma unroll
+        for (int r = 0; r < kR; r++) {
+            const long long i = b0 + r * 32 + lane;
+            ok[r] = i < cnt;
+            w[r] = ok[r] ? __ldcg(lst + i) : 0;
+        }
+        measure_rows<kR>(p, sh, C, slot, ok, g, w, acc_b, acc_e);
     }
     for (int o = 16; o > 0; o >>= 1) {
         acc_b += __shfl_down_sync(kFull, acc_b, o);
@@ -645,7 +693,7 @@ __device__ void relax_general(const KParams &p, const Shared &sh, const int32_t 
         bool found = false;
         if ((todo >> q2) & 1ull) {
             uint64_t *Pw = p.P + (size_t)q2 * p.W + wi;
-            if (!(__ldcg(Pw) & bit)) {
+            if (!(__ldca(Pw) & bit)) {
                 const unsigned long long old = atomicOr((unsigned long long *)Pw, bit);
                 found = !(old & bit);
             }
@@ -676,11 +724,15 @@ __device__ __forceinline__ void relax_batch(const KParams &p, const Shared &sh, 
     uint64_t *Pq = p.P + (size_t)q2 * p.W;
     bool act[kR];
     uint64_t pw[kR];
-    const bool pre = sh.flags[0] != 0;  // on big levels most targets are visited: test first
+    // on big levels most targets are visited: test first.  The test may be
+    // served from L1 (hub words are read by many warps): P only gains bits
+    // during a launch, so a stale copy can only miss bits, and the atomicOr
+    // decides
+    const bool pre = sh.flags[0] != 0;
 #pragma unroll
     for (int r = 0; r < kR; r++) {
         act[r] = valid[r] && ((tm[r] >> q2) & 1ull);
-        pw[r] = (act[r] && pre) ? __ldcg(Pq + ((uint32_t)w[r] >> 6)) : (act[r] ? 0ull : ~0ull);
+        pw[r] = (act[r] && pre) ? __ldca(Pq + ((uint32_t)w[r] >> 6)) : (act[r] ? 0ull : ~0ull);
     }
 #pragma unroll
     for (int r = 0; r < kR; r++) {
@@ -966,7 +1018,7 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
 #pragma unroll
         for (int h = 0; h < kPullRows; h++)
             cand[h] = cand[h] && re[h] > rb[h] &&
-                      !((__ldcg(p.P + (size_t)uq2 * p.W + ((uint32_t)w[h] >> 6)) >> (w[h] & 63)) &
+                      !((__ldca(p.P + (size_t)uq2 * p.W + ((uint32_t)w[h] >> 6)) >> (w[h] & 63)) &
                         1ull);
         // up to kWarpRow in-neighbours of each row, kPullBatch at a time:
         // their ids, then their frontier bits, every row's batch together
@@ -1257,7 +1309,7 @@ __device__ __forceinline__ int gate_wait(const KParams &p, unsigned &seen) {
                     beat = b;
                     t0 = now;
                 } else if (now - t0 > kBarrierTimeoutNs) {
-                    atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_TIMEOUT);
+                    set_status(p.c, (int32_t)RPQ_ERR_TIMEOUT);
                     break;
                 }
             }
@@ -1326,7 +1378,7 @@ __device__ __forceinline__ bool park_wait(const KParams &p, unsigned long long e
                         break;
                     }
                     if (global_timer_ns() - t0 > kBarrierTimeoutNs) {
-                        atomicCAS(&p.c->status, 0, (int32_t)RPQ_ERR_TIMEOUT);
+                        set_status(p.c, (int32_t)RPQ_ERR_TIMEOUT);
                         ok = 0;
                         break;
                     }
@@ -1768,7 +1820,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             }
         }
         __syncthreads();
-        measure_level(p, sh, s_gsf, sh.cv[1], 0, 0, 1, s_acc);
+        measure_level(p, sh, sh.cv[1], 0, 0, 1, s_acc);
         __syncthreads();
         if (p.trace && threadIdx.x == 0)
             p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
@@ -1843,12 +1895,12 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         // level j+1 is complete: measure the rows of its pairs, then plan it
         if (grid) {
             if (!grid_barrier(p.c)) return;
-            measure_level(p, sh, s_gsf, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
+            measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
                           s_acc);
             if (!grid_barrier(p.c)) return;
         } else {
             __syncthreads();
-            measure_level(p, sh, s_gsf, sh.cv[1], (j + 1) % 3, 0, 1, s_acc);
+            measure_level(p, sh, sh.cv[1], (j + 1) % 3, 0, 1, s_acc);
             __syncthreads();
             heartbeat(p);
             if (load_status(p.c) != 0) return;
@@ -2353,7 +2405,8 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
         cudaMemsetAsync(ws->ctr.p, 0, sizeof(Counters), st);
         RPQ_CUDA_TRY(cudaStreamSynchronize(st));
         ws->dirty = true;
-        const rpq_status e = hc->status != 0 ? (rpq_status)hc->status : RPQ_ERR_CUDA;
+        const int32_t hs_status = status_of(hc->gen_status);
+        const rpq_status e = hs_status != 0 ? (rpq_status)hs_status : RPQ_ERR_CUDA;
         ws_release(g, std::move(ws));
         return fail(e, "device traversal failed (status %d)", (int)e);
     }
@@ -2647,11 +2700,11 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     Counters hc;
     RPQ_CUDA_TRY(cudaMemcpyAsync(&hc, p.c, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hc.status != 0) {
+    if (const int32_t hs_status = status_of(hc.gen_status)) {
         // a traversal that gave up leaves the barrier counters mid-way: reset them
         cudaMemsetAsync(p.c, 0, sizeof(Counters), st);
         cudaStreamSynchronize(st);
-        return fail((rpq_status)hc.status, "device traversal failed (status %d)", hc.status);
+        return fail((rpq_status)hs_status, "device traversal failed (status %d)", hs_status);
     }
     *out_count = hc.answer_count;
     if (hc.answer_count > capacity)
