@@ -156,6 +156,7 @@ struct KParams {
     int32_t solo_items;  // its frontier items <= this and no unit pulls (solo_mass < 0: never)
     uint32_t epoch;      // distinct per launch on this workspace (tags the gate word)
     int32_t clear_first; // P and F hold garbage: clear them before the traversal
+    int32_t disc_cap;    // a CTA measures its own discoveries when at most this many (<= kDisc)
     // automaton tables (device)
     const QGroup *groups;
     const QUnit *units;
@@ -198,8 +199,14 @@ __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsign
 }
 
 // ------------------------------------------------------------ barrier ----
+constexpr unsigned long long kStatusMask = (1ull << 30) - 1;
+// set in the barrier word when some CTA discovered more pairs in a level
+// than its shared-memory buffer holds (the level is then measured again
+// from the visited lists)
+constexpr unsigned long long kOverflowBit = 1ull << 30;
+
 __host__ __device__ __forceinline__ int32_t status_of(unsigned long long gen_status) {
-    return (int32_t)(uint32_t)gen_status;
+    return (int32_t)(gen_status & kStatusMask);
 }
 
 __device__ __forceinline__ int load_status(const Counters *c) {
@@ -211,13 +218,15 @@ __device__ __forceinline__ void set_status(Counters *c, int32_t err) {
     unsigned long long old = *(volatile unsigned long long *)&c->gen_status;
     while (status_of(old) == 0) {
         const unsigned long long seen =
-            atomicCAS(&c->gen_status, old, (old & ~0xffffffffull) | (uint32_t)err);
+            atomicCAS(&c->gen_status, old, (old & ~kStatusMask) | (uint32_t)err);
         if (seen == old) break;
         old = seen;  // a barrier moved the generation on: try again
     }
 }
 
-__device__ __forceinline__ bool grid_barrier(Counters *c) {
+// Grid barrier: -1 when the query failed, else 1 when some CTA flagged a
+// discovery-buffer overflow before arriving, else 0.
+__device__ __forceinline__ int grid_sync(Counters *c) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -245,11 +254,13 @@ __device__ __forceinline__ bool grid_barrier(Counters *c) {
                 }
             }
         }
-        s_ok = status_of(w) == 0;
+        s_ok = status_of(w) != 0 ? -1 : (w & kOverflowBit) ? 1 : 0;
     }
     __syncthreads();
-    return s_ok != 0;
+    return s_ok;
 }
+
+__device__ __forceinline__ bool grid_barrier(Counters *c) { return grid_sync(c) >= 0; }
 
 // ------------------------------------------------------- shared layout ---
 // Per-query tables live in shared memory for the whole kernel, so that the
@@ -465,11 +476,21 @@ __device__ __forceinline__ int32_t row_skew(const int32_t *nbr, int32_t rb) {
     return (int32_t)(((uintptr_t)(nbr + rb) >> 2) & 3);
 }
 
+// Pairs a CTA discovers in one level, kept in its shared memory as well as
+// in the visited lists, so that the CTA measures them itself as soon as its
+// expansion ends (no grid barrier, no list reads); more than this in one CTA
+// sends the level to the grid-wide measure pass over the lists.
+constexpr int kDisc = 4096;
+__shared__ int32_t s_dw[kDisc];  // the vertices
+__shared__ uint8_t s_dq[kDisc];  // their states
+__shared__ int s_nd;             // pairs discovered by this CTA in the level
+
 // Lanes with found[r] have discovered the new pair (q2, w[r]) of the next
 // level: appended to the visited list of q2 (one reservation for the warp)
-// and, on grid levels, its frontier bit set.  The rows the pair will expand
-// are measured after the level (measure_level), with many lookups in flight
-// instead of one chain per discovery.  q2 warp-uniform; all 32 lanes call.
+// and to the CTA's discovery buffer, and, on grid levels, its frontier bit
+// set.  The rows the pair will expand are measured after the level
+// (measure_buffer), with many lookups in flight instead of one chain per
+// discovery.  q2 warp-uniform; all 32 lanes call.
 template <int kB>
 __device__ __forceinline__ void warp_discover_batch(const KParams &p, const LevelCtx &L,
                                                     const bool (&found)[kB], int q2,
@@ -484,15 +505,25 @@ __device__ __forceinline__ void warp_discover_batch(const KParams &p, const Leve
     if (!total) return;
     const unsigned lane = lane_id();
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)total);
+    int pos = 0;
+    if (lane == 0) {
+        base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)total);
+        pos = atomicAdd(&s_nd, total);
+    }
     base = __shfl_sync(kFull, base, 0);
+    pos = __shfl_sync(kFull, pos, 0);
     int32_t *lst = L.VL + (size_t)q2 * p.n + L.vnext[q2];
     uint64_t *Fq = L.F ? L.F + (size_t)q2 * p.W : nullptr;
-    unsigned long long run = base;
+    int run = 0;
 #pragma unroll
     for (int r = 0; r < kB; r++) {
         if (found[r]) {
-            lst[run + __popc(m[r] & lanemask_lt())] = w[r];
+            const int k = run + __popc(m[r] & lanemask_lt());
+            lst[base + k] = w[r];
+            if (pos + k < kDisc) {
+                s_dw[pos + k] = w[r];
+                s_dq[pos + k] = (uint8_t)q2;
+            }
             if (Fq)
                 atomicOr((unsigned long long *)(Fq + ((uint32_t)w[r] >> 6)), 1ull << (w[r] & 63));
         }
@@ -596,6 +627,37 @@ __device__ __forceinline__ void measure_rows(const KParams &p, const Shared &sh,
     }
 }
 
+// End of a measure pass on this CTA: its sums of push bytes / product edges
+// (per lane in acc_b / acc_e) and of edge mass per group go to counter slot
+// `slot` of C.
+__device__ __forceinline__ void measure_flush(const KParams &p, const Shared &sh, const Ctrs &C,
+                                              int slot, unsigned long long *s_acc,
+                                              unsigned long long acc_b, unsigned long long acc_e) {
+    const unsigned lane = lane_id();
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_b += __shfl_down_sync(kFull, acc_b, o);
+        acc_e += __shfl_down_sync(kFull, acc_e, o);
+    }
+    if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
+    __syncthreads();
+    if (lane == 0) {
+        if (acc_b) atomicAdd(&s_acc[0], acc_b);
+        if (acc_e) atomicAdd(&s_acc[1], acc_e);
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
+        const unsigned long long v = sh.s_mf[g];
+        if (v) {
+            atomicAdd(&C.mf[slot * C.mstride + g], v);
+            sh.s_mf[g] = 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (s_acc[0]) atomicAdd(&C.bytes[slot], s_acc[0]);
+        if (s_acc[1]) atomicAdd(&C.edges[slot], s_acc[1]);
+    }
+}
+
 // After level j: measures the rows of every pair it discovered (level j+1's
 // frontier: VL[q][vnext[q], vnext[q] + n_q), n_q in counter slot `slot` of
 // C), on CTA `cta` of `ncta`.  The work is (group, batch of 32 x kR pairs)
@@ -653,27 +715,55 @@ __device__ void measure_level(const KParams &p, const Shared &sh, const Ctrs &C,
         }
         measure_rows<kR>(p, sh, C, slot, ok, g, w, acc_b, acc_e);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        acc_b += __shfl_down_sync(kFull, acc_b, o);
-        acc_e += __shfl_down_sync(kFull, acc_e, o);
+    measure_flush(p, sh, C, slot, s_acc, acc_b, acc_e);
+}
+
+// Measures the pairs this CTA discovered in the level (its buffer, s_nd <=
+// kDisc of them) into counter slot `slot` of C: (batch of 32 x kR buffered
+// pairs, group) units dealt round-robin to the CTA's warps, each lane's
+// pairs of the group's source state measured together.
+__device__ bool measure_buffer(const KParams &p, const Shared &sh, const Ctrs &C, int slot,
+                               unsigned long long *s_acc) {
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    const int nd = s_nd;    // read by every thread before anyone resets it
+    if (nd > p.disc_cap) {  // CTA-uniform
+        __syncthreads();
+        if (threadIdx.x == 0) s_nd = 0;
+        return false;
     }
-    if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
-    __syncthreads();
-    if (lane == 0) {
-        if (acc_b) atomicAdd(&s_acc[0], acc_b);
-        if (acc_e) atomicAdd(&s_acc[1], acc_e);
-    }
-    __syncthreads();
-    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) {
-        const unsigned long long v = sh.s_mf[g];
-        if (v) {
-            atomicAdd(&C.mf[slot * C.mstride + g], v);
-            sh.s_mf[g] = 0;
+    const int nunits = (nd + 32 * kR - 1) / (32 * kR) * p.n_groups;
+    unsigned long long acc_b = 0, acc_e = 0;
+    for (int u = warp; u < nunits; u += kWarps) {
+        const int b = u / p.n_groups, g = u - b * p.n_groups;
+        const int q = sh.gq[g];
+        bool ok[kR];
+        int32_t w[kR];
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < kR; r++) {
+            const int i = b * 32 * kR + r * 32 + (int)lane;
+            ok[r] = i < nd && s_dq[i] == q;
+            w[r] = ok[r] ? s_dw[i] : 0;
+            any = any || ok[r];
         }
+        if (!__any_sync(kFull, any)) continue;
+        measure_rows<kR>(p, sh, C, slot, ok, g, w, acc_b, acc_e);
     }
+    measure_flush(p, sh, C, slot, s_acc, acc_b, acc_e);
+    if (threadIdx.x == 0) s_nd = 0;
+    return true;
+}
+
+// CTA 0, when some CTA's buffer overflowed: counter slot `slot` forgets
+// the partial measurements before the grid measures the level from the
+// lists, and the flag is cleared.
+__device__ __forceinline__ void measure_reset(const KParams &p, const Shared &sh, int slot) {
+    const Ctrs &C = sh.cv[0];
+    for (int g = threadIdx.x; g < p.n_groups; g += kThreads) C.mf[slot * C.mstride + g] = 0;
     if (threadIdx.x == 0) {
-        if (s_acc[0]) atomicAdd(&C.bytes[slot], s_acc[0]);
-        if (s_acc[1]) atomicAdd(&C.edges[slot], s_acc[1]);
+        C.rows[slot] = C.srows[slot] = C.bytes[slot] = C.edges[slot] = 0;
+        atomicAnd(&p.c->gen_status, ~kOverflowBit);
     }
 }
 
@@ -1772,6 +1862,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         s_gsf[threadIdx.x] = lo;
     }
     if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_nd = 0;
     __syncthreads();
     if (p.clear_first) {
         const size_t words = (size_t)p.S * p.W;
@@ -1820,7 +1911,8 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             }
         }
         __syncthreads();
-        measure_level(p, sh, sh.cv[1], 0, 0, 1, s_acc);
+        if (!measure_buffer(p, sh, sh.cv[1], 0, s_acc))
+            measure_level(p, sh, sh.cv[1], 0, 0, 1, s_acc);
         __syncthreads();
         if (p.trace && threadIdx.x == 0)
             p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
@@ -1894,13 +1986,25 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         trace_put(p, j, 1, global_timer_ns());
         // level j+1 is complete: measure the rows of its pairs, then plan it
         if (grid) {
-            if (!grid_barrier(p.c)) return;
-            measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
-                          s_acc);
-            if (!grid_barrier(p.c)) return;
+            // every CTA measures what it discovered, from its buffer; if a
+            // buffer overflowed, the grid measures the level again from the
+            // lists
+            __syncthreads();
+            if (!measure_buffer(p, sh, sh.cv[0], (j + 1) % 3, s_acc) && threadIdx.x == 0)
+                atomicOr(&p.c->gen_status, kOverflowBit);
+            const int r = grid_sync(p.c);
+            if (r < 0) return;
+            if (r > 0) {
+                if (lead) measure_reset(p, sh, (j + 1) % 3);
+                if (!grid_barrier(p.c)) return;
+                measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
+                              s_acc);
+                if (!grid_barrier(p.c)) return;
+            }
         } else {
             __syncthreads();
-            measure_level(p, sh, sh.cv[1], (j + 1) % 3, 0, 1, s_acc);
+            if (!measure_buffer(p, sh, sh.cv[1], (j + 1) % 3, s_acc))
+                measure_level(p, sh, sh.cv[1], (j + 1) % 3, 0, 1, s_acc);
             __syncthreads();
             heartbeat(p);
             if (load_status(p.c) != 0) return;
@@ -2332,6 +2436,8 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
     p.solo_mass = (int32_t)env_float("RPQ_SOLO_MASS", (float)g->solo_mass);
     p.solo_items = (int32_t)env_float("RPQ_SOLO_ITEMS", (float)g->solo_items);
+    // a smaller limit (tests) sends more levels down the grid-wide measure pass
+    p.disc_cap = std::min(kDisc, std::max(0, (int)env_float("RPQ_DISCOVERY_BUFFER", (float)kDisc)));
     p.epoch = ++ws->epoch;
     p.clear_first = ws->dirty ? 1 : 0;
     QueryResult *hr = reinterpret_cast<QueryResult *>(hs + kResultOffset);
@@ -2665,6 +2771,7 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
     p.solo_mass = g->solo_mass;
     p.solo_items = g->solo_items;
+    p.disc_cap = kDisc;
     // the scratch layout moves with the automaton's size: clear P / F first
     p.clear_first = 1;
     p.groups = reinterpret_cast<const QGroup *>(base + x_tab + o_groups);

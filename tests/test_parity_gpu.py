@@ -352,6 +352,38 @@ def test_solo_levels_and_workspace_reuse(solo, pull_mode, monkeypatch):
         assert gpu_regex(gg, t, 4, s).tolist() == o["answer"].tolist(), (t, s)
 
 
+@pytest.mark.parametrize("cap", [0, 7, 4096], ids=["buffer_0", "buffer_7", "buffer_default"])
+@pytest.mark.parametrize("solo", [SOLO[0], SOLO[2]], ids=["grid_only", "solo_max"])
+def test_discovery_buffer_and_list_fallback(cap, solo, monkeypatch):
+    """Each CTA measures the pairs it discovered from its own shared-memory
+    buffer; when a buffer overflows (forced here with a small limit) the
+    level is measured again from the visited lists, by the grid or by CTA 0
+    alone.  Answers and counters must equal the oracle's either way."""
+    import torch
+
+    monkeypatch.setenv("RPQ_DISCOVERY_BUFFER", str(cap))
+    monkeypatch.setenv("RPQ_SOLO_MASS", str(solo[0]))
+    monkeypatch.setenv("RPQ_SOLO_ITEMS", str(solo[1]))
+    g = W.rmat_graph(14, 1 << 18, 4, seed=67)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    texts = ["0*", "(0|^1)*/2", "1/(0|2)*", "(0/1)*", "^3/(1|2)+"]
+    srcs = W.below(68, 1, 10, g.n).tolist()
+    for i, s in enumerate(srcs):
+        t = texts[i % len(texts)]
+        nfa = R.rpq_nfa_compile(t, 4)
+        got, st = R.rpq_query(gg, nfa, s, with_stats=True)
+        e = nfa.export()
+        same = Nfa(e["n_states"], 4, list(zip(e["from"].tolist(), e["label"].tolist(),
+                                                e["to"].tolist())), e["starts"], e["finals"])
+        o = og.ssr(same, s)
+        assert got.tolist() == o["answer"].tolist(), (t, s)
+        check_counters(st, o["counters"])
+        dev = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        k = R.rpq_query(gg, nfa, s, out=dev)
+        assert dev[:k].cpu().numpy().tolist() == o["answer"].tolist(), (t, s)
+
+
 def test_last_answer_two_call_pattern():
     """A host buffer that is too small gets RPQ_ERR_CAPACITY with the full
     count; rpq_last_answer then hands over the whole answer without a second
