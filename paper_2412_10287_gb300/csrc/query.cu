@@ -757,14 +757,11 @@ __device__ bool measure_buffer(const KParams &p, const Shared &sh, const Ctrs &C
 
 // CTA 0, when some CTA's buffer overflowed: counter slot `slot` forgets
 // the partial measurements before the grid measures the level from the
-// lists, and the flag is cleared.
+// lists.
 __device__ __forceinline__ void measure_reset(const KParams &p, const Shared &sh, int slot) {
     const Ctrs &C = sh.cv[0];
     for (int g = threadIdx.x; g < p.n_groups; g += kThreads) C.mf[slot * C.mstride + g] = 0;
-    if (threadIdx.x == 0) {
-        C.rows[slot] = C.srows[slot] = C.bytes[slot] = C.edges[slot] = 0;
-        atomicAnd(&p.c->gen_status, ~kOverflowBit);
-    }
+    if (threadIdx.x == 0) C.rows[slot] = C.srows[slot] = C.bytes[slot] = C.edges[slot] = 0;
 }
 
 // General relaxation (any number of target states per lane): edge (., w)
@@ -1997,6 +1994,9 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             if (r > 0) {
                 if (lead) measure_reset(p, sh, (j + 1) % 3);
                 if (!grid_barrier(p.c)) return;
+                // every CTA has left the barrier that saw the flag: clear it
+                // now (earlier, a CTA still waiting there could miss it)
+                if (lead && threadIdx.x == 0) atomicAnd(&p.c->gen_status, ~kOverflowBit);
                 measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
                               s_acc);
                 if (!grid_barrier(p.c)) return;

@@ -125,3 +125,22 @@ def test_batch_errors_and_capacity():
     one = R.rpq_query(gg, nfas[0], 0)
     assert offs[1] - offs[0] == one.size
     assert R.rpq_query_batch(gg, [], []) == []
+
+
+@pytest.mark.parametrize("cap", [0, 64], ids=["buffer_0", "buffer_64"])
+def test_batch_with_discovery_buffer_overflow(cap, monkeypatch):
+    """Concurrent query kernels (slots engine) whose CTAs' discovery buffers
+    overflow on most levels, so that the levels are measured again from the
+    visited lists while other queries run beside them: every answer equals
+    the oracle's."""
+    monkeypatch.setenv("RPQ_DISCOVERY_BUFFER", str(cap))
+    g = W.rmat_graph(14, 1 << 18, 4, seed=37)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    texts = ["0*", "(0|^1)*/2", "1/(0|2)*", "(0/1)*", "^3/(1|2)+", "2/^2"]
+    srcs = W.below(38, 1, 96, g.n).tolist()
+    nfas = [R.rpq_nfa_compile(texts[i % len(texts)], 4) for i in range(96)]
+    got = R.rpq_query_batch(gg, nfas, srcs)
+    for i in range(96):
+        exp = og.ssr(oracle_compile(texts[i % len(texts)], 4), srcs[i])["answer"]
+        assert got[i].tolist() == exp.tolist(), i
