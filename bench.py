@@ -373,15 +373,19 @@ def run_batch(args, R, torch):
         batch_once()
         seq_once()
     tb, ts = [], []
+    batch_launches = 0
     for _ in range(args.steps):
         for fn, acc in ((batch_once, tb), (seq_once, ts)):
             flush.fill_(1)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0 = R.rpq_kernel_launches()
             e0.record(stream)
             fn()
             e1.record(stream)
             torch.cuda.synchronize()
+            if fn is batch_once:
+                batch_launches += R.rpq_kernel_launches() - k0
             acc.append(e0.elapsed_time(e1) / 1000.0)
     qb = len(nfas) * args.steps / sum(tb)
     qs = len(nfas) * args.steps / sum(ts)
@@ -442,7 +446,7 @@ def run_batch(args, R, torch):
             "sequential_single_queries_per_s": qs, "batch_speedup": qb / qs,
             "engine": os.environ.get("RPQ_BATCH_ENGINE", "auto (slots for mixed automata)"),
             "other_engines_queries_per_s": extra,
-            "answer_vertices_per_step": int(total), "gpu_launches": None}
+            "answer_vertices_per_step": int(total), "gpu_launches": batch_launches}
     print(json.dumps(line), flush=True)
 
 
@@ -487,7 +491,9 @@ def run_serve(args, R, torch):
     served_stats = {}
     for name, cfg in engines.items():
         srv = R.Server(gg, **cfg)
+        k0 = R.rpq_kernel_launches()
         served_stats[name] = served(srv)
+        served_stats[name]["gpu_launches"] = R.rpq_kernel_launches() - k0
         srv.close()
     st_srv = served_stats["slots"]
 
@@ -533,7 +539,9 @@ def run_serve(args, R, torch):
                                    "templates of 1-12 DFA states); server engine 0 = 8 "
                                    "concurrent query slots (value), engine 1 = 256 bit lanes"},
             "p50_ms": st_srv["p50_ms"], "p99_ms": st_srv["p99_ms"],
-            "engines": {k: {"qps": v["qps"], "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"]}
+            "gpu_launches": st_srv["gpu_launches"],
+            "engines": {k: {"qps": v["qps"], "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"],
+                            "gpu_launches": v["gpu_launches"]}
                         for k, v in served_stats.items()},
             "unbatched_served_loop": unb,
             "saturation_queries_per_s": {"server_slots": sat["slots"],
@@ -629,6 +637,7 @@ def main():
     torch.cuda.synchronize()
 
     step_ms, recs = [], []
+    k_timed = 0
     with ClockSampler(dev) as clk:
         for _ in range(args.steps):
             flush.fill_(1)
@@ -637,10 +646,12 @@ def main():
                 torch.distributed.barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            k0 = R.rpq_kernel_launches()
             e0.record(stream)
             recs.extend(one_step(True))
             e1.record(stream)
             torch.cuda.synchronize()
+            k_timed += R.rpq_kernel_launches() - k0
             step_ms.append(e0.elapsed_time(e1))
     clocks = clk.summary()
     total_s = sum(step_ms) / 1000.0
@@ -699,7 +710,7 @@ def main():
                          "avg_launch_ms": avg_launch_s * 1000.0},
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": nq * args.steps,
+            "gpu_launches": k_timed,
             "clocks": clocks,
         }
         if cpu:

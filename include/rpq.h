@@ -301,6 +301,12 @@ const char *rpq_last_error(void);
 /* Library version, e.g. "0.1.0". */
 const char *rpq_version(void);
 
+/* Kernels this library has launched since the process loaded it, over every
+ * thread, device and entry point (a replayed lane level step counts each of
+ * its kernels).  Never fails; monotone.  Callers take the difference around
+ * a region of interest. */
+uint64_t rpq_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,8 @@ bool is_device_pointer(const void *p) {
 
 void count_object(int delta) { g_live_objects += delta; }
 
+std::atomic<unsigned long long> g_kernel_launches{0};
+
 }  // namespace rpq
 
 using namespace rpq;
@@ -75,6 +77,10 @@ using namespace rpq;
 extern "C" const char *rpq_last_error(void) { return t_error.c_str(); }
 
 extern "C" const char *rpq_version(void) { return "0.1.0"; }
+
+extern "C" uint64_t rpq_kernel_launches(void) {
+    return (uint64_t)g_kernel_launches.load(std::memory_order_relaxed);
+}
 
 extern "C" rpq_status rpq_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *),
                                         void *ctx) {

@@ -100,6 +100,7 @@ rpq_status device_exclusive_scan(const T *in, int64_t *out, int64_t n, int64_t *
     if (!part.alloc(sizeof(int64_t) * (nb + 1)) || !part_scan.alloc(sizeof(int64_t) * (nb + 1)))
         return fail(RPQ_ERR_OOM, "scan temporaries");
     scan_tiles_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, part.as<int64_t>());
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     // scan the tile sums (recursively) into part_scan[0..nb], part_scan[nb] = total
     if (nb == 1) {
@@ -111,9 +112,11 @@ rpq_status device_exclusive_scan(const T *in, int64_t *out, int64_t n, int64_t *
                                                       nb, part_scan.as<int64_t>() + nb, st);
         if (s != RPQ_OK) return s;
         scan_add_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, part_scan.as<int64_t>());
+        note_launch();
         RPQ_CUDA_TRY(cudaGetLastError());
     }
     copy_total_kernel<<<1, 1, 0, st>>>(out, part_scan.as<int64_t>(), nb, total_dev);
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     // temporaries are freed when this returns: make sure the kernels are done
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -354,6 +357,7 @@ rpq_status radix_sort3(int32_t *k[3], int32_t *t[3], const int bits[3], int64_t 
         for (int shift = 0; shift < bits[a]; shift += 8) {
             radix_hist_kernel<<<(unsigned)nb, kSortThreads, 0, st>>>(cur[a], m, shift, nb,
                                                                     hist.as<int32_t>());
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
             rpq_status s = device_exclusive_scan<int32_t>(hist.as<int32_t>(), offs.as<int64_t>(),
                                                           256 * nb, total.as<int64_t>(), st);
@@ -361,6 +365,7 @@ rpq_status radix_sort3(int32_t *k[3], int32_t *t[3], const int bits[3], int64_t 
             radix_scatter_kernel<<<(unsigned)nb, kSortThreads, 0, st>>>(
                 cur[a], shift, m, nb, offs.as<int64_t>(), cur[0], cur[1], cur[2], alt[0], alt[1],
                 alt[2]);
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
             std::swap(cur[0], alt[0]);
             std::swap(cur[1], alt[1]);
@@ -392,12 +397,14 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
         return fail(RPQ_ERR_OOM, "graph build temporaries");
     if (m > 0) {
         row_flags_kernel<<<grid_for(m), 256, 0, st>>>(lab, maj, m, rf.as<int32_t>());
+        note_launch();
         RPQ_CUDA_TRY(cudaGetLastError());
         rpq_status s = device_exclusive_scan<int32_t>(rf.as<int32_t>(), rscan.as<int64_t>(), m,
                                                       rtot.as<int64_t>(), st);
         if (s != RPQ_OK) return s;
     }
     label_start_kernel<<<grid_for(m + 1), 256, 0, st>>>(lab, m, L, lstart.as<int64_t>());
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     std::vector<int64_t> start(L + 1);
     RPQ_CUDA_TRY(cudaMemcpyAsync(start.data(), lstart.p, sizeof(int64_t) * (L + 1),
@@ -410,6 +417,7 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
         rows_per_label_kernel<<<grid_for(L), 256, 0, st>>>(rscan.as<int64_t>(), rf.as<int32_t>(),
                                                            lstart.as<int64_t>(), L,
                                                            drows.as<int64_t>());
+        note_launch();
         RPQ_CUDA_TRY(cudaGetLastError());
         RPQ_CUDA_TRY(cudaMemcpyAsync(rows.data(), drows.p, sizeof(int64_t) * L,
                                      cudaMemcpyDeviceToHost, st));
@@ -452,6 +460,7 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
             int32_t *off = dense_buf.as<int32_t>() + dpos;
             dense_offsets_kernel<<<grid_for(A.nnz + 1), 256, 0, st>>>(maj, start[a], start[a + 1],
                                                                      n, off);
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
             A.off = off;
             A.nrows = n;
@@ -462,6 +471,7 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
             hyper_rows_kernel<<<grid_for(A.nnz), 256, 0, st>>>(maj, rf.as<int32_t>(),
                                                               rscan.as<int64_t>(), start[a],
                                                               start[a + 1], rw, off);
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
             A.rows = rw;
             A.off = off;
@@ -469,6 +479,7 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
             const int64_t nb = (((int64_t)n - 1) >> bbits[a]) + 1;
             int32_t *bk = bkt_buf.as<int32_t>() + bpos;
             bucket_index_kernel<<<grid_for(nb + 1), 256, 0, st>>>(rw, A.nrows, bbits[a], nb, bk);
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
             A.bkt = bk;
             A.bbits = bbits[a];
@@ -532,6 +543,7 @@ extern "C" rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64
         check_ids_kernel<<<grid_for(m), 256, 0, st>>>(k1.as<int32_t>(), k2.as<int32_t>(),
                                                      k0.as<int32_t>(), m, n_vertices, n_labels,
                                                      bad.as<int32_t>());
+        note_launch();
         RPQ_CUDA_TRY(cudaGetLastError());
     }
     int32_t h_bad = 0;
@@ -571,6 +583,7 @@ extern "C" rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64
         int64_t mu = 0;
         if (m > 0) {
             flags_kernel<<<grid_for(m), 256, 0, st>>>(r[0], r[1], r[2], m, o[0]);
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
             rpq_status s = device_exclusive_scan<int32_t>(o[0], pos.as<int64_t>(), m,
                                                           tot.as<int64_t>(), st);
@@ -586,6 +599,7 @@ extern "C" rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64
             compact_kernel<<<grid_for(m), 256, 0, st>>>(r[0], r[1], r[2], m, o[0],
                                                         pos.as<int64_t>(), o[1], o[2],
                                                         nb->as<int32_t>());
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
         }
         g->m_unique = mu;
@@ -603,6 +617,7 @@ extern "C" rpq_status rpq_graph_load(int32_t n_vertices, int32_t n_labels, int64
             if (A.fmt == ADJ_EMPTY) continue;
             long_rows_kernel<<<grid_for(A.nrows), 256, 0, st>>>(
                 A, rpq_graph::kLongRow, rpq_graph::kLongChunk, lr.as<unsigned long long>() + 3 * d);
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
         }
         std::vector<unsigned long long> h(3 * nd);
@@ -673,6 +688,7 @@ extern "C" rpq_status rpq_graph_export(const rpq_graph *g, int32_t label, int32_
     DevBuf d;
     if (!d.alloc(sizeof(int64_t) * ((size_t)g->n + 1))) return fail(RPQ_ERR_OOM, "export buffer");
     export_dense_kernel<<<grid_for((int64_t)g->n + 1), 256>>>(A, g->n, d.as<int64_t>());
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     RPQ_CUDA_TRY(cudaMemcpy(offsets, d.p, sizeof(int64_t) * ((size_t)g->n + 1),
                             cudaMemcpyDeviceToHost));

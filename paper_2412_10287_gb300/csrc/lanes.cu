@@ -699,6 +699,8 @@ rpq_status lane_capture_step(const LParams &p, LaneStepOut *out_dev, cudaStream_
     const size_t smem = lane_smem(p.K);
     cudaGraph_t graph;
     RPQ_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    // captured, not launched: each replay of the graph launches these
+    // kLaneStepKernels
     lane_step_vertices_kernel<<<sms * 4, kLThreads, smem, st>>>(p);
     lane_step_hubs_kernel<<<sms * 4, kLThreads, smem, st>>>(p);
     lane_step_commit_kernel<<<sms * 8, kLThreads, 0, st>>>(p);
@@ -714,6 +716,7 @@ rpq_status lane_seed(const LParams &p, const int32_t *seeds_dev, int n_seeds,
                      const int32_t *verts_dev, int n_verts, int step, cudaStream_t st) {
     if (n_seeds == 0 && n_verts == 0) return RPQ_OK;
     lane_seed_step_kernel<<<1, 256, 0, st>>>(p, seeds_dev, n_seeds, verts_dev, n_verts, step);
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     return RPQ_OK;
 }
@@ -734,12 +737,14 @@ rpq_status lane_harvest_impl(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
     uint64_t *Mcur = (cur_step & 1) ? p.M1 : p.M0;
     lane_extract_kernel<<<152 * 8, 256, 0, st>>>(p.P, Mcur, g->n, p.K, fmask_dev, lane_row_dev,
                                                  ws->A32.as<uint32_t>(), words32, clear ? 1 : 0);
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     offsets_host->assign((size_t)count + 1, 0);
     if (count == 0) return RPQ_OK;
     const long long nblk = (long long)count * chunks;
     lane_count_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count,
                                                      chunks, ws->cnt.as<int64_t>());
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     rpq_status s = device_exclusive_scan<int64_t>(ws->cnt.as<int64_t>(), ws->pos.as<int64_t>(),
                                                   nblk, ws->pos.as<int64_t>() + nblk, st);
@@ -757,6 +762,7 @@ rpq_status lane_harvest_impl(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
             lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count,
                                                                chunks, ws->pos.as<int64_t>(), out_dev,
                                                                capacity);
+            note_launch();
             RPQ_CUDA_TRY(cudaGetLastError());
         }
         return RPQ_OK;
@@ -766,6 +772,7 @@ rpq_status lane_harvest_impl(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
     lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(ws->A32.as<uint32_t>(), words32, count, chunks,
                                                        ws->pos.as<int64_t>(), tmp.as<int32_t>(),
                                                        total);
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     answers_host->resize((size_t)total);
     RPQ_CUDA_TRY(cudaMemcpyAsync(answers_host->data(), tmp.p, sizeof(int32_t) * total,
@@ -901,6 +908,7 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
         cudaEventDestroy(e1);
         return fail(RPQ_ERR_CUDA, "lane kernel launch: %s", cudaGetErrorString(le));
     }
+    note_launch();
     cudaEventRecord(e1, st);
     LaneCounters hc;
     RPQ_CUDA_TRY(cudaMemcpyAsync(&hc, ws->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -958,6 +966,7 @@ rpq_status bitsets_to_lists(const uint32_t *bits, int64_t words32, int count, in
         return fail(RPQ_ERR_OOM, "answer compaction buffers");
     lane_count_kernel<<<(unsigned)nblk, 256, 0, st>>>(bits, words32, count, chunks,
                                                      cnt.as<int64_t>());
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     rpq_status s = device_exclusive_scan<int64_t>(cnt.as<int64_t>(), pos.as<int64_t>(), nblk,
                                                   pos.as<int64_t>() + nblk, st);
@@ -973,6 +982,7 @@ rpq_status bitsets_to_lists(const uint32_t *bits, int64_t words32, int count, in
     if (out_is_dev) {
         lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(bits, words32, count, chunks,
                                                            pos.as<int64_t>(), out, capacity);
+        note_launch();
         RPQ_CUDA_TRY(cudaGetLastError());
         RPQ_CUDA_TRY(cudaStreamSynchronize(st));
         return RPQ_OK;
@@ -981,6 +991,7 @@ rpq_status bitsets_to_lists(const uint32_t *bits, int64_t words32, int count, in
     if (!tmp.alloc(sizeof(int32_t) * total)) return fail(RPQ_ERR_OOM, "answer staging");
     lane_write_kernel<<<(unsigned)nblk, 256, 0, st>>>(bits, words32, count, chunks,
                                                        pos.as<int64_t>(), tmp.as<int32_t>(), total);
+    note_launch();
     RPQ_CUDA_TRY(cudaGetLastError());
     RPQ_CUDA_TRY(cudaMemcpyAsync(out, tmp.p, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, st));
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));

@@ -85,6 +85,9 @@ struct LaneWorkspace : WorkspaceBase {
     ~LaneWorkspace() override;
 };
 
+// Kernels in one captured lane level step (one replay launches them all).
+constexpr int kLaneStepKernels = 4;
+
 // ---- lane engine entry points used by the server (lanes.cu) ----
 rpq_status lane_ws_acquire_fixed(rpq_graph *g, int K, std::unique_ptr<LaneWorkspace> *out);
 void lane_ws_return(rpq_graph *g, std::unique_ptr<LaneWorkspace> w);

@@ -2500,6 +2500,7 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     void *args[] = {&p};
     RPQ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)rpq_query_kernel, dim3(grid),
                                              dim3(kThreads), args, smem, st));
+    note_launch();
     if (timed) RPQ_CUDA_TRY(cudaEventRecord(ws->ev1, st));
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));
     if (*(volatile uint32_t *)&hr->epoch != p.epoch) {
@@ -2804,6 +2805,7 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     void *args[] = {&p};
     RPQ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)rpq_query_kernel, dim3(grid),
                                              dim3(kThreads), args, smem, st));
+    note_launch();
     Counters hc;
     RPQ_CUDA_TRY(cudaMemcpyAsync(&hc, p.c, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     RPQ_CUDA_TRY(cudaStreamSynchronize(st));

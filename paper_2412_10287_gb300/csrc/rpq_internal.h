@@ -3,6 +3,7 @@
 
 #include <cstdarg>
 #include <cstddef>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -12,6 +13,11 @@
 #include "rpq.h"
 
 namespace rpq {
+
+// Kernels this library has launched in this process (every thread and
+// device), read by rpq_kernel_launches.
+extern std::atomic<unsigned long long> g_kernel_launches;
+inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------- errors --
 // Records a message for rpq_last_error() on this thread and returns `st`.

@@ -246,9 +246,11 @@ void worker_main(rpq_server *s) {
         // one level step for every lane
         if (err == RPQ_OK) {
             cudaError_t e = cudaGraphLaunch(s->step_exec, s->st);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess) {
+                g_kernel_launches.fetch_add(kLaneStepKernels, std::memory_order_relaxed);
                 e = cudaMemcpyAsync(s->out_host, s->step_out.p, sizeof(LaneStepOut),
                                     cudaMemcpyDeviceToHost, s->st);
+            }
             if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
             if (e != cudaSuccess) err = fail(RPQ_ERR_CUDA, "level step: %s", cudaGetErrorString(e));
             else if (s->out_host->status != 0) err = (rpq_status)s->out_host->status;

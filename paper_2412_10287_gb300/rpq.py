@@ -36,7 +36,7 @@ EXPORTED = (
     "rpq_query_bitset",
     "rpq_query_batch", "rpq_serve_create", "rpq_serve_submit", "rpq_serve_poll",
     "rpq_serve_drain", "rpq_serve_stats_get", "rpq_serve_destroy", "rpq_last_error",
-    "rpq_version",
+    "rpq_version", "rpq_kernel_launches",
 )
 
 
@@ -122,6 +122,8 @@ def lib():
             getattr(L, name).restype = None
         L.rpq_last_error.restype = ctypes.c_char_p
         L.rpq_version.restype = ctypes.c_char_p
+        L.rpq_kernel_launches.argtypes = []
+        L.rpq_kernel_launches.restype = ctypes.c_uint64
         _LIB = L
     return _LIB
 
@@ -480,3 +482,8 @@ def rpq_version() -> str:
 
 def rpq_last_error() -> str:
     return lib().rpq_last_error().decode(errors="replace")
+
+
+def rpq_kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().rpq_kernel_launches())

@@ -36,6 +36,14 @@ def test_header_symbols_exported():
         assert hasattr(L, n), n
 
 
+def test_kernel_launch_counter_without_gpu():
+    """The launch counter needs no device: compiling automata launches
+    nothing, so it does not move."""
+    a = R.rpq_kernel_launches()
+    R.rpq_nfa_compile("0/1*", 2)
+    assert R.rpq_kernel_launches() == a >= 0
+
+
 def test_version_and_errors():
     assert R.rpq_version().count(".") == 2
     with pytest.raises(R.RpqError) as e:

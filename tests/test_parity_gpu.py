@@ -384,6 +384,28 @@ def test_discovery_buffer_and_list_fallback(cap, solo, monkeypatch):
         assert dev[:k].cpu().numpy().tolist() == o["answer"].tolist(), (t, s)
 
 
+def test_kernel_launch_counter():
+    """Each single query is one cooperative launch of the traversal kernel,
+    whatever its answer size or number of levels; a failed argument check
+    launches nothing."""
+    import torch
+
+    g = W.rmat_graph(13, 1 << 16, 4, seed=69)
+    gg = load(g)
+    dev = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    srcs = W.below(70, 1, 6, g.n).tolist()
+    nfa = R.rpq_nfa_compile("(0|^1)*/2", 4)
+    a = R.rpq_kernel_launches()
+    for s in srcs:
+        R.rpq_query(gg, nfa, s, out=dev)
+        R.rpq_query(gg, nfa, s)
+    assert R.rpq_kernel_launches() - a == 2 * len(srcs)
+    a = R.rpq_kernel_launches()
+    with pytest.raises(R.RpqError):
+        R.rpq_query(gg, nfa, g.n)  # source out of range
+    assert R.rpq_kernel_launches() == a
+
+
 def test_last_answer_two_call_pattern():
     """A host buffer that is too small gets RPQ_ERR_CAPACITY with the full
     count; rpq_last_answer then hands over the whole answer without a second
