@@ -465,7 +465,7 @@ def run_serve(args, R, torch):
         if q.regex not in nfas:
             nfas[q.regex] = R.rpq_nfa_compile(q.regex, g.n_labels)
     qs = w.queries
-    engines = {"slots": dict(max_lanes=8, engine=0), "lanes": dict(max_lanes=256, max_states=16,
+    engines = {"slots": dict(max_lanes=12, engine=0), "lanes": dict(max_lanes=256, max_states=16,
                                                                     engine=1)}
     for cfg in engines.values():  # warm-up burst
         srv = R.Server(gg, **cfg)
@@ -536,7 +536,7 @@ def run_serve(args, R, torch):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"rmat20_serve: Poisson arrivals at 2,000 q/s for "
                                    f"{args.serve_seconds + 1.0:.0f} s ({len(qs)} queries, mixed "
-                                   "templates of 1-12 DFA states); server engine 0 = 8 "
+                                   "templates of 1-12 DFA states); server engine 0 = 12 "
                                    "concurrent query slots (value), engine 1 = 256 bit lanes"},
             "p50_ms": st_srv["p50_ms"], "p99_ms": st_srv["p99_ms"],
             "gpu_launches": st_srv["gpu_launches"],

@@ -243,7 +243,7 @@ rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_nfa *const *
 
 typedef struct rpq_serve_config {
     int32_t max_lanes;       /* queries in flight on the device: query slots for engine 0
-                                (0 = 8, at most 64), bit lanes for engine 1 (0 = 256) */
+                                (0 = 12, at most 64), bit lanes for engine 1 (0 = 256) */
     int32_t max_states;      /* state slots per lane, engine 1 (0 = 16) */
     int32_t queue_capacity;  /* submitted-but-not-admitted queries (0 = 65536) */
     int64_t memory_budget;   /* bytes of device state the server may hold (0 = no limit) */

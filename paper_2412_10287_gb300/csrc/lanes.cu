@@ -1097,7 +1097,7 @@ extern "C" rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_n
     const bool use_lanes = eng ? strcmp(eng, "lanes") == 0 : shared;
     if (!use_lanes) {
         const char *sl = getenv("RPQ_SLOTS");
-        const int slots = std::max(1, std::min(64, sl ? atoi(sl) : 8));
+        const int slots = std::max(1, std::min(64, sl ? atoi(sl) : kDefaultSlots));
         for (int i = 0; i < n; i++)
             if (sources[i] < 0 || sources[i] >= gm->n)
                 return fail(RPQ_ERR_INVALID, "query %d: source %d outside [0, %d)", i, sources[i],

@@ -85,6 +85,10 @@ struct LaneWorkspace : WorkspaceBase {
     ~LaneWorkspace() override;
 };
 
+// Concurrent query slots of the slots engine by default: 12 kernels of
+// 1/12 of the grid each (measured best of 4-16 on the mixed rmat20 batch).
+constexpr int kDefaultSlots = 12;
+
 // Kernels in one captured lane level step (one replay launches them all).
 constexpr int kLaneStepKernels = 4;
 

@@ -386,7 +386,7 @@ extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_confi
     if (cfg) c = *cfg;
     if (c.engine != 0 && c.engine != 1) return fail(RPQ_ERR_INVALID, "engine must be 0 or 1");
     if (c.engine == 0) {
-        const int slots = c.max_lanes ? c.max_lanes : 8;
+        const int slots = c.max_lanes ? c.max_lanes : kDefaultSlots;
         if (slots <= 0 || slots > 64) return fail(RPQ_ERR_INVALID, "max_lanes (slots) must be in [1, 64]");
         if (c.max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
         std::unique_ptr<rpq_server> s(new rpq_server());
