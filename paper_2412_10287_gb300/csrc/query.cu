@@ -200,10 +200,15 @@ __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsign
 
 // ------------------------------------------------------------ barrier ----
 constexpr unsigned long long kStatusMask = (1ull << 30) - 1;
-// set in the barrier word when some CTA discovered more pairs in a level
+// Set in the barrier word when some CTA discovered more pairs in a level
 // than its shared-memory buffer holds (the level is then measured again
-// from the visited lists)
-constexpr unsigned long long kOverflowBit = 1ull << 30;
+// from the visited lists): bit 30 + (g & 1) for the barrier that closes
+// generation g, so that a CTA still leaving barrier g cannot mistake a
+// flag raised for barrier g + 1 for its own.
+__host__ __device__ __forceinline__ unsigned long long overflow_bit(unsigned gen) {
+    return 1ull << (30 + (gen & 1u));
+}
+constexpr unsigned long long kOverflowBits = 3ull << 30;
 
 __host__ __device__ __forceinline__ int32_t status_of(unsigned long long gen_status) {
     return (int32_t)(gen_status & kStatusMask);
@@ -224,16 +229,17 @@ __device__ __forceinline__ void set_status(Counters *c, int32_t err) {
     }
 }
 
-// Grid barrier: -1 when the query failed, else 1 when some CTA flagged a
-// discovery-buffer overflow before arriving, else 0.
-__device__ __forceinline__ int grid_sync(Counters *c) {
+// Grid barrier: -1 when the query failed, else 1 when some CTA (this one
+// with `overflow`) flagged a discovery-buffer overflow on arriving, else 0.
+__device__ __forceinline__ int grid_sync(Counters *c, bool overflow = false) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         // arrive with release semantics (this CTA's writes, ordered by the
         // __syncthreads above), leave with acquire semantics
         unsigned long long w = *(volatile unsigned long long *)&c->gen_status;
-        const unsigned gen = (unsigned)(w >> 32);
+        const unsigned gen = (unsigned)(w >> 32);  // cannot move on before this CTA arrives
+        if (overflow) atomicOr(&c->gen_status, overflow_bit(gen));
         unsigned arrived;
         asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&c->bar_count) : "memory");
         if (arrived == gridDim.x - 1) {
@@ -254,7 +260,7 @@ __device__ __forceinline__ int grid_sync(Counters *c) {
                 }
             }
         }
-        s_ok = status_of(w) != 0 ? -1 : (w & kOverflowBit) ? 1 : 0;
+        s_ok = status_of(w) != 0 ? -1 : (w & overflow_bit(gen)) ? 1 : 0;
     }
     __syncthreads();
     return s_ok;
@@ -1987,16 +1993,17 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             // buffer overflowed, the grid measures the level again from the
             // lists
             __syncthreads();
-            if (!measure_buffer(p, sh, sh.cv[0], (j + 1) % 3, s_acc) && threadIdx.x == 0)
-                atomicOr(&p.c->gen_status, kOverflowBit);
-            const int r = grid_sync(p.c);
+            const bool fits = measure_buffer(p, sh, sh.cv[0], (j + 1) % 3, s_acc);
+            const int r = grid_sync(p.c, !fits);
             if (r < 0) return;
             if (r > 0) {
                 if (lead) measure_reset(p, sh, (j + 1) % 3);
                 if (!grid_barrier(p.c)) return;
                 // every CTA has left the barrier that saw the flag: clear it
-                // now (earlier, a CTA still waiting there could miss it)
-                if (lead && threadIdx.x == 0) atomicAnd(&p.c->gen_status, ~kOverflowBit);
+                // now (earlier, a CTA still waiting there could miss it); the
+                // other parity's bit is clear, the barrier just passed takes
+                // no flags
+                if (lead && threadIdx.x == 0) atomicAnd(&p.c->gen_status, ~kOverflowBits);
                 measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
                               s_acc);
                 if (!grid_barrier(p.c)) return;
