@@ -1,20 +1,29 @@
 #!/usr/bin/env python
 """Benchmark: single-source 2-RPQ queries/s on one GB300 (or N replicas).
 
-Workload (default ``rmat20``): R-MAT scale 20 (1,048,576 vertices, 2^24 edge
-samples, a=0.57 b=c=0.19), 8 labels with Zipf(1.0) frequencies, seed 1; 400
-queries = templates a*, a.b*, (a|b)*.c, a^-.b* x 100 random sources with
-non-zero degree; queries run one at a time, as in the paper's evaluation
-(section 5.3: data preloaded, sequential isolated queries).
+Default workload ``kb20m``, the largest single-GPU configuration: a
+knowledge-base-shaped Chung-Lu graph (20,000,000 vertices, 200,000,000
+edges, out-degree exponent 2.1, 500 labels with Zipf(1.1) frequencies,
+seed 2) and 200 single-source queries (8 templates x 25 random sources with
+non-zero degree: a.b*.c, (a|b^-)+, a*.b*, chains, (a.b)*, a.(b|c^-)*.d),
+run one at a time as in the paper's evaluation (section 5.3: data
+preloaded, sequential isolated queries).
 
-One step = those 400 queries.  ``value`` = queries/s with the graph and the
+One step = those 200 queries.  ``value`` = queries/s with the graph and the
 outputs resident on the device (rpq_query with a device output buffer,
 CUDA events on the launching stream around each step, L2 flushed between
 steps).  ``e2e`` = the same queries through the public API with host
 output buffers and regex compilation inside the timed region.  The roofline
-line refers to the traversal kernel (one cooperative launch per query).
+object refers to the traversal kernel (one cooperative launch per query).
+
+The same line carries, under ``extras``, the other configurations on the
+R-MAT scale-20 graph: 400 single queries one at a time (``rmat20``), 256
+mixed queries per rpq_query_batch call against the same queries one at a
+time (``batch``), and a Poisson stream of 2,000 queries/s through the
+server against the unbatched served loop (``serve``).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload kb20m|rmat20|batch|serve] [--no-extras]
 """
 
 from __future__ import annotations
@@ -36,7 +45,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-PROFILE_JSON = os.path.join(ROOT, "profiles", "rpq_query_kernel_rmat20.json")
+PROFILE_JSON = os.path.join(ROOT, "profiles", "rpq_query_kernel_kb20m.json")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2412_10287_gb300", "csrc", "query.cu")
 
 
@@ -50,15 +59,25 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "kb20m", "batch", "serve"],
-                    help="rmat20: single queries (the default line); kb20m: single queries on "
-                         "the 20M-vertex knowledge-base graph; batch: 256 mixed queries per "
-                         "launch; serve: Poisson arrivals through the server")
+    ap.add_argument("--workload", default="kb20m", choices=["kb20m", "rmat20", "batch", "serve"],
+                    help="kb20m: single queries on the 20M-vertex knowledge-base graph (the "
+                         "default line); rmat20: single queries on the R-MAT scale-20 graph; "
+                         "batch: 256 mixed queries per launch; serve: Poisson arrivals through "
+                         "the server")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the rmat20 / batch / serve figures of the default line")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--one-query", default=None,
                     help="profiling case: run this regex once for warm-up and once more "
                          "(with --source) on the workload's graph, print its counters, exit")
     ap.add_argument("--source", type=int, default=0)
+    ap.add_argument("--profile-sample", type=int, default=0, metavar="N",
+                    help="profiling case: run the workload's queries once, then again only "
+                         "the N with the most algorithmic bytes (the launches to capture), "
+                         "and write their algorithmic bytes to --sample-out; exit")
+    ap.add_argument("--sample-out", default="gpurun_out/profile_sample.json")
+    ap.add_argument("--sample-json", default=None,
+                    help="with --write-profile: the --profile-sample file of the capture")
     ap.add_argument("--write-profile", default=None, metavar="NCU_CSV",
                     help="read an ncu CSV of traversal-kernel launches taken with --metrics "
                          "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum and "
@@ -86,14 +105,20 @@ def sha256(path):
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def profile_traffic():
+def profile_traffic(alg_bytes_per_launch=None):
     """Per-launch DRAM bytes of the traversal kernel from the committed ncu
-    summary, or None if absent or taken on a different kernel source."""
+    summary, or None if absent or taken on a different kernel source.  A
+    summary taken on a sample of launches holds their DRAM bytes per
+    algorithmic byte; that ratio times `alg_bytes_per_launch` (this run's
+    mean) is the traffic of a mean launch."""
     try:
         with open(PROFILE_JSON) as f:
             pj = json.load(f)
         if pj.get("kernel_source_sha256") != sha256(KERNEL_SOURCE):
             return None
+        ratio = pj.get("dram_per_algorithmic_byte")
+        if ratio is not None and alg_bytes_per_launch is not None:
+            return ratio * alg_bytes_per_launch
         return pj.get("dram_bytes_per_launch")
     except Exception:
         return None
@@ -113,10 +138,13 @@ def ncu_value(unit, value):
     return v
 
 
-def write_profile(csv_path, workload_name):
+def write_profile(csv_path, workload_name, sample_json=None):
     """Per-launch DRAM bytes and ncu durations of the traversal kernel, from an
     ncu CSV, written beside the kernel source's hash so that a later change
-    to the kernel voids the figure."""
+    to the kernel voids the figure.  With `sample_json` (written by
+    --profile-sample: the algorithmic bytes of each captured launch, in
+    launch order) the summary also holds DRAM bytes per algorithmic byte
+    over the sample, which scales the traffic to any run's mean launch."""
     import csv
 
     launches = {}
@@ -127,8 +155,9 @@ def write_profile(csv_path, workload_name):
             continue
         d = launches.setdefault(row["ID"], {})
         d[row["Metric Name"]] = ncu_value(row.get("Metric Unit", ""), row["Metric Value"])
-    per = [d for d in launches.values()
-           if "dram__bytes_read.sum" in d and "dram__bytes_write.sum" in d]
+    ids = sorted(launches, key=lambda k: int(k))
+    per = [launches[k] for k in ids
+           if "dram__bytes_read.sum" in launches[k] and "dram__bytes_write.sum" in launches[k]]
     if not per:
         raise SystemExit(f"no rpq_query_kernel launches with DRAM metrics in {csv_path}")
     rd = sum(d["dram__bytes_read.sum"] for d in per) / len(per)
@@ -142,6 +171,18 @@ def write_profile(csv_path, workload_name):
         "ncu_ms_per_launch": (sum(dur) / len(dur) * 1e3) if dur else None,
         "note": "ncu flushes caches before each profiled launch: cold-cache figures",
     }
+    if sample_json:
+        with open(sample_json) as f:
+            sj = json.load(f)
+        alg = sj["algorithmic_bytes"]
+        if len(alg) != len(per):
+            raise SystemExit(f"{len(per)} captured launches, {len(alg)} sample queries")
+        dram = [d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"] for d in per]
+        out["sample"] = sj.get("sample")
+        out["sample_algorithmic_bytes_per_launch"] = sum(alg) / len(alg)
+        out["sample_push_bytes_per_launch"] = sum(sj["push_bytes"]) / len(alg)
+        out["dram_per_algorithmic_byte"] = sum(dram) / sum(alg)
+        out["dram_per_push_byte"] = sum(dram) / max(1, sum(sj["push_bytes"]))
     path = os.path.join(ROOT, "profiles", f"rpq_query_kernel_{workload_name}.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
@@ -206,7 +247,7 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def workload(per_template, name="rmat20"):
+def workload(per_template, name="kb20m"):
     from paper_2412_10287_gb300 import workloads as W
 
     if name == "kb20m":
@@ -216,6 +257,12 @@ def workload(per_template, name="rmat20"):
 
 # query templates, seed and label skew of each single-query workload
 QUERY_SPECS = {"rmat20": ("TEMPLATES_SMALL", 1, 1.0), "kb20m": ("TEMPLATES_KB", 2, 1.1)}
+# sources per template of each single-query workload (one step)
+PER_TEMPLATE = {"rmat20": 100, "kb20m": 25}
+
+
+def per_template_for(name, requested=None):
+    return requested if requested else PER_TEMPLATE[name]
 
 
 def rank_queries(g, name, per_template, rank):
@@ -274,61 +321,100 @@ def autotune(R, gg, g, name):
             "sample": f"{len(sample)} queries of the same templates, seed 99"}
 
 
-def oracle_sample(w, seconds_budget, max_threads=None):
-    """Times the CPU oracle (as it stands) on a stratified sample of the
-    workload's queries, on the host cores (one query per thread)."""
+def oracle_graph(w):
     from oracle import oracle as O
+
+    g = w.graph
+    return O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+
+
+def oracle_sample(w, seconds_budget, og=None, max_threads=None, offset=0):
+    """Times the CPU oracle (as it stands) on a bounded sample of the
+    workload's queries, on the host cores (one query per thread).  The
+    sample walks the queries in a fixed interleaved order (every template
+    in turn), starting at `offset`; a query is submitted only while the
+    elapsed time is under `seconds_budget` (the first one always), so the
+    wall time is the budget plus at most the queries still running then.  Returns queries/s over
+    the queries done and what the sample was."""
     from oracle.regex_nfa import compile_regex
 
     g = w.graph
-    og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+    own = og is None
+    if own:
+        og = oracle_graph(w)
     threads = max_threads or len(os.sched_getaffinity(0))
     qs = w.queries
-    # estimate the per-query cost on a small probe, then size the sample
-    probe = [qs[i] for i in range(0, len(qs), max(1, len(qs) // 8))][:8]
+    # interleaved order: query k of template 0, of template 1, ... then k+1
+    by_tpl = {}
+    for q in qs:
+        by_tpl.setdefault(q.template, []).append(q)
+    order = [lst[k] for k in range(max(len(v) for v in by_tpl.values()))
+             for lst in by_tpl.values() if k < len(lst)]
+    order = order[offset % len(order):] + order[:offset % len(order)]
+    done = []
     t0 = time.perf_counter()
-    for q in probe:
+
+    def run(q):
         og.ssr(compile_regex(q.regex, g.n_labels), q.source)
-    per_q = (time.perf_counter() - t0) / max(1, len(probe))
-    n_sample = int(max(threads, min(len(qs), seconds_budget / max(per_q, 1e-6))))
-    stride = max(1, len(qs) // n_sample)
-    sample = qs[::stride][:n_sample]
-    nfas = [compile_regex(q.regex, g.n_labels) for q in sample]
+        return q
 
-    def run(i):
-        return og.ssr(nfas[i], sample[i].source)["counters"]["answer"]
-
-    t0 = time.perf_counter()
+    it = iter(order)
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(run, range(len(sample))))
+        running = set()
+        while True:
+            while len(running) < threads and (time.perf_counter() - t0 < seconds_budget
+                                              or not (done or running)):
+                q = next(it, None)
+                if q is None:
+                    break
+                running.add(ex.submit(run, q))
+            if not running:
+                break
+            fin, running = cf.wait(running, return_when=cf.FIRST_COMPLETED)
+            done.extend(f.result() for f in fin)
     wall = time.perf_counter() - t0
-    og.close()
-    return {"value": len(sample) / wall, "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(sample)} of the {len(qs)} queries (every {stride}th), "
-                      f"{threads} threads, one query per thread; adjacency lists built before "
-                      f"timing; {wall:.1f} s wall"}
+    if own:
+        og.close()
+    return {"value": len(done) / wall, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "queries": len(done), "wall_s": wall,
+            "sample": f"{len(done)} of the {len(qs)} queries (templates interleaved, from "
+                      f"position {offset % len(order)}), {threads} threads, one query per "
+                      f"thread; adjacency lists built before timing; {wall:.1f} s wall"}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the same workload,
+    metric and unit as the GPU line, each step a bounded sample."""
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    w = workload(args.per_template)
-    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    name = args.workload if args.workload in QUERY_SPECS else "kb20m"
+    w = workload(per_template_for(name, args.per_template), name)
+    og = oracle_graph(w)
+    per_step = max(2.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
     vals = []
+    offset = 0
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(w, per_step_budget * 4)
+        r = oracle_sample(w, per_step, og=og, offset=offset)
+        offset += r["queries"]
         if i >= args.warmup:
             vals.append(r)
-    v = statistics.median([r["value"] for r in vals])
+    og.close()
+    nq = sum(r["queries"] for r in vals)
+    wall = sum(r["wall_s"] for r in vals)
+    v = nq / wall
     line = {"impl": "reference", "metric": "rpq_queries_per_s", "value": v, "unit": "queries/s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * len(w.queries) / v, "higher_is_better": True,
+            "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": workload_config(w, len(w.queries),
-                                      {"note": "CPU oracle timed on a bounded sample per step"}),
+                                      {"note": "CPU oracle; each step a bounded sample of the "
+                                               f"workload's queries ({per_step:.0f} s budget); "
+                                               "ms_per_step is the wall time of the samples run"}),
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": vals[-1]["cores"],
-                             "kind": "oracle", "sample": vals[-1]["sample"]},
+                             "kind": "oracle",
+                             "sample": f"{nq} queries over {len(vals)} timed steps; last step: "
+                                       + vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -336,14 +422,16 @@ def run_reference(args):
 
 # ------------------------------------------------------ batch / serve ----
 
-def run_batch(args, R, torch):
-    """256 mixed queries (2-12 DFA states) per rpq_query_batch launch against
-    the same 256 queries run one at a time."""
+def run_batch(args, R, torch, g=None, gg=None):
+    """256 mixed queries (2-12 DFA states) per rpq_query_batch call against
+    the same 256 queries run one at a time.  Returns the figures."""
+    import ctypes
+
     from paper_2412_10287_gb300 import workloads as W
 
-    g = W.config2_graph()
+    g = g or W.config2_graph()
     w = W.config4(g, 256)
-    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    gg = gg or R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
     nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
     srcs = [q.source for q in w.queries]
     states = [n.info()[0] for n in nfas]
@@ -351,8 +439,6 @@ def run_batch(args, R, torch):
     total = sum(a.size for a in res)
     out = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
     offs = np.zeros(len(nfas) + 1, np.int64)
-    import ctypes
-
     handles = (ctypes.c_void_p * len(nfas))(*[x.h.value for x in nfas])
     src_arr = np.array(srcs, np.int32)
     stream = torch.cuda.current_stream()
@@ -363,8 +449,9 @@ def run_batch(args, R, torch):
                                     ctypes.c_void_p(stream.cuda_stream))
         assert s == 0, R.rpq_last_error()
 
+    one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
     def seq_once():
-        one = torch.empty(g.n, dtype=torch.int32, device="cuda")
         for nfa, s in zip(nfas, srcs):
             R.rpq_query(gg, nfa, s, out=one, stream=stream)
 
@@ -392,6 +479,8 @@ def run_batch(args, R, torch):
     # the same batch forced onto bit lanes, and a shared-automaton batch (one
     # automaton from 256 sources: the multi-source BFS case lanes are made for)
     extra = {}
+    shared = [R.rpq_nfa_compile("0*", g.n_labels)] * len(srcs)
+    sh_handles = (ctypes.c_void_p * len(shared))(*[x.h.value for x in shared])
     for label, env, jobs in (("mixed_on_lanes", "lanes", None),
                              ("shared_automaton_lanes", None, "shared"),
                              ("shared_automaton_sequential", None, "shared_seq")):
@@ -402,8 +491,6 @@ def run_batch(args, R, torch):
             if jobs is None:
                 fn = batch_once
             else:
-                shared = [R.rpq_nfa_compile("0*", g.n_labels)] * len(srcs)
-                sh_handles = (ctypes.c_void_p * len(shared))(*[x.h.value for x in shared])
                 sh_res = R.rpq_query_batch(gg, shared, srcs)
                 sh_out = torch.empty(max(1, sum(a.size for a in sh_res)), dtype=torch.int32,
                                      device="cuda")
@@ -416,7 +503,6 @@ def run_batch(args, R, torch):
                         assert st_ == 0, R.rpq_last_error()
                 else:
                     def fn():
-                        one = torch.empty(g.n, dtype=torch.int32, device="cuda")
                         for s_ in srcs:
                             R.rpq_query(gg, shared[0], s_, out=one, stream=stream)
             fn()
@@ -435,31 +521,25 @@ def run_batch(args, R, torch):
                     os.environ.pop("RPQ_BATCH_ENGINE", None)
                 else:
                     os.environ["RPQ_BATCH_ENGINE"] = old_env
-    line = {"metric": "rpq_queries_per_s", "value": qb, "unit": "queries/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * sum(tb) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "rmat20_batch: the rmat20 graph; 256 mixed queries per "
-                                   f"rpq_query_batch call (DFA states {min(states)}-{max(states)}); "
-                                   "seed 3",
-                       "l2": "flushed between steps (256 MiB write)"},
+    return {"workload": "rmat20_batch: the rmat20 graph; 256 mixed queries per rpq_query_batch "
+                        f"call (DFA states {min(states)}-{max(states)}); seed 3",
+            "queries_per_s": qb, "ms_per_step": 1000.0 * sum(tb) / args.steps,
             "sequential_single_queries_per_s": qs, "batch_speedup": qb / qs,
             "engine": os.environ.get("RPQ_BATCH_ENGINE", "auto (slots for mixed automata)"),
             "other_engines_queries_per_s": extra,
-            "answer_vertices_per_step": int(total), "gpu_launches": batch_launches}
-    print(json.dumps(line), flush=True)
+            "answer_vertices_per_step": int(total), "gpu_launches": batch_launches,
+            "l2": "flushed between steps (256 MiB write)"}
 
 
-def run_serve(args, R, torch):
+def run_serve(args, R, torch, g=None, gg=None):
     """Poisson arrivals (2,000 q/s) replayed in real time into the server, and
-    into a one-at-a-time served loop; then both at saturation."""
-    import threading
-
+    into a one-at-a-time served loop; then both at saturation.  Returns the
+    figures."""
     from paper_2412_10287_gb300 import workloads as W
 
-    g = W.config2_graph()
+    g = g or W.config2_graph()
     w = W.config5(g, rate=2000.0, duration_s=args.serve_seconds, warmup_s=1.0)
-    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    gg = gg or R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
     nfas = {}
     for q in w.queries:
         if q.regex not in nfas:
@@ -530,16 +610,12 @@ def run_serve(args, R, torch):
     for q in qs[:sat_n]:
         R.rpq_query(gg, nfas[q.regex], q.source, out=out, stream=stream)
     sat_seq = sat_n / (time.perf_counter() - t0)
-
-    line = {"metric": "rpq_served_queries_per_s", "value": st_srv["qps"], "unit": "queries/s",
-            "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"rmat20_serve: Poisson arrivals at 2,000 q/s for "
-                                   f"{args.serve_seconds + 1.0:.0f} s ({len(qs)} queries, mixed "
-                                   "templates of 1-12 DFA states); server engine 0 = 12 "
-                                   "concurrent query slots (value), engine 1 = 256 bit lanes"},
-            "p50_ms": st_srv["p50_ms"], "p99_ms": st_srv["p99_ms"],
-            "gpu_launches": st_srv["gpu_launches"],
+    return {"workload": f"rmat20_serve: Poisson arrivals at 2,000 q/s for "
+                        f"{args.serve_seconds + 1.0:.0f} s ({len(qs)} queries, mixed templates "
+                        "of 1-12 DFA states); server engine 0 = 12 concurrent query slots "
+                        "(queries_per_s), engine 1 = 256 bit lanes",
+            "queries_per_s": st_srv["qps"], "p50_ms": st_srv["p50_ms"],
+            "p99_ms": st_srv["p99_ms"], "gpu_launches": st_srv["gpu_launches"],
             "engines": {k: {"qps": v["qps"], "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"],
                             "gpu_launches": v["gpu_launches"]}
                         for k, v in served_stats.items()},
@@ -547,10 +623,154 @@ def run_serve(args, R, torch):
             "saturation_queries_per_s": {"server_slots": sat["slots"],
                                          "server_lanes": sat["lanes"],
                                          "one_at_a_time": sat_seq, "queries": sat_n}}
-    print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------- GPU path ---
+
+def measure_single(R, torch, w, gg, nfas, srcs, steps, warmup, stream, clock_dev=None,
+                   dist=None):
+    """Times `steps` steps of the workload's queries run one at a time with
+    device outputs (CUDA events around each step on the launching stream, L2
+    flushed in between).  Returns the per-step times, the per-query records
+    (host latency, stats, states), the launches counted and the clocks."""
+    out = torch.empty(w.graph.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_step(collect):
+        res = []
+        for nfa, s in zip(nfas, srcs):
+            t0 = time.perf_counter()
+            cnt, st = R.rpq_query(gg, nfa, s, out=out, stream=stream, with_stats=True)
+            if collect:
+                res.append((time.perf_counter() - t0, st, nfa.info()[0]))
+        return res
+
+    for _ in range(warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+    step_ms, recs, k_timed = [], [], 0
+    clk = ClockSampler(clock_dev) if clock_dev is not None else None
+    if clk:
+        clk.__enter__()
+    try:
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            k0 = R.rpq_kernel_launches()
+            e0.record(stream)
+            recs.extend(one_step(True))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            k_timed += R.rpq_kernel_launches() - k0
+            step_ms.append(e0.elapsed_time(e1))
+    finally:
+        if clk:
+            clk.__exit__(None, None, None)
+    return {"step_ms": step_ms, "recs": recs, "launches": k_timed,
+            "clocks": clk.summary() if clk else None}
+
+
+def latency_summary(recs):
+    lat = sorted(r[0] * 1000.0 for r in recs)
+    return lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+
+def algorithmic_bytes(recs, W_words):
+    """Push-model bytes and the dense formulation's bitset sweeps (3 x S x W
+    x 8 bytes per expanded level) of the recorded queries."""
+    push = sum(r[1]["push_bytes"] for r in recs)
+    sweep = sum(3 * r[2] * W_words * 8 * (r[1]["levels"] + 1) for r in recs)
+    return push, sweep
+
+
+def run_rmat20_extra(args, R, torch, g, gg):
+    """The rmat20 single-query figures (400 queries one at a time) for the
+    default line's extras."""
+    from paper_2412_10287_gb300 import workloads as W
+
+    qs = W.make_queries(g, W.TEMPLATES_SMALL, 100, seed=1, zipf_s=1.0)
+    nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in qs]
+    srcs = [q.source for q in qs]
+    stream = torch.cuda.current_stream()
+    m = measure_single(R, torch, W.Workload("rmat20", g, qs), gg, nfas, srcs, args.steps,
+                       args.warmup, stream)
+    total_s = sum(m["step_ms"]) / 1000.0
+    p50, p99 = latency_summary(m["recs"])
+    push, sweep = algorithmic_bytes(m["recs"], (g.n + 63) // 64)
+    launch_s = sum(r[1]["device_ms"] for r in m["recs"]) / len(m["recs"]) / 1000.0
+    peak, _ = measured_peak()
+    ach = (push + sweep) / len(m["recs"]) / launch_s / 1e9
+    return {"workload": "rmat20: R-MAT scale 20, 8 labels Zipf(1.0), seed 1; 400 single-source "
+                        "queries (a*, a.b*, (a|b)*.c, a^-.b*), one at a time",
+            "queries_per_s": len(qs) * args.steps / total_s, "p50_ms": p50, "p99_ms": p99,
+            "ms_per_step": 1000.0 * total_s / args.steps,
+            "product_edges_per_s": sum(r[1]["product_edges"] for r in m["recs"]) / total_s,
+            "roofline": {"achieved": ach, "frac": ach / peak, "unit": "GB/s",
+                         "avg_launch_ms": launch_s * 1000.0,
+                         "achieved_push_bytes_only": push / len(m["recs"]) / launch_s / 1e9},
+            "gpu_launches": m["launches"]}
+
+
+def run_extras(args, R, torch):
+    """rmat20, batch and serve figures on the R-MAT scale-20 graph."""
+    from paper_2412_10287_gb300 import workloads as W
+
+    g = W.config2_graph()
+    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    out = {"rmat20": run_rmat20_extra(args, R, torch, g, gg),
+           "batch": run_batch(args, R, torch, g, gg),
+           "serve": run_serve(args, R, torch, g, gg)}
+    gg.close()
+    return out
+
+
+def run_profile_sample(args):
+    """The launches an ncu DRAM capture takes: every query of the workload
+    once (skipped by the capture: `-s` = the number of queries), then the
+    `--profile-sample` queries with the most algorithmic bytes again, whose
+    algorithmic and push-model bytes go to `--sample-out`.  The push/pull
+    setting is the library's default or the RPQ_PULL_* / RPQ_SOLO_*
+    environment variables (no autotuning launches before the capture)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2412_10287_gb300 import rpq as R
+
+    name = args.workload
+    w = workload(per_template_for(name, args.per_template), name)
+    g = w.graph
+    gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    W_words = (g.n + 63) // 64
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
+    alg = []
+    for nfa, q in zip(nfas, w.queries):
+        _, st = R.rpq_query(gg, nfa, q.source, out=out, stream=stream, with_stats=True)
+        S = nfa.info()[0]
+        alg.append((st["push_bytes"] + 3 * S * W_words * 8 * (st["levels"] + 1), st["push_bytes"]))
+    pick = sorted(range(len(alg)), key=lambda i: -alg[i][0])[:args.profile_sample]
+    for i in pick:
+        R.rpq_query(gg, nfas[i], w.queries[i].source, out=out, stream=stream)
+    torch.cuda.synchronize()
+    rec = {"workload": name, "skip_launches": len(nfas),
+           "queries": [[w.queries[i].regex, w.queries[i].source] for i in pick],
+           "algorithmic_bytes": [alg[i][0] for i in pick],
+           "push_bytes": [alg[i][1] for i in pick],
+           "sample": f"the {len(pick)} of the {len(nfas)} {name} queries with the most "
+                     "algorithmic bytes, captured after one pass over all of them"}
+    os.makedirs(os.path.dirname(os.path.abspath(args.sample_out)), exist_ok=True)
+    with open(args.sample_out, "w") as f:
+        json.dump(rec, f)
+    print(json.dumps(rec))
+
 
 def main():
     args = parse()
@@ -558,7 +778,10 @@ def main():
         run_reference(args)
         return
     if args.write_profile:
-        write_profile(args.write_profile, args.workload)
+        write_profile(args.write_profile, args.workload, args.sample_json)
+        return
+    if args.profile_sample:
+        run_profile_sample(args)
         return
     if args.one_query is not None:
         import torch
@@ -586,11 +809,20 @@ def main():
         __graft_entry__.build()
         from paper_2412_10287_gb300 import rpq as R
 
-        (run_batch if args.workload == "batch" else run_serve)(args, R, torch)
+        r = (run_batch if args.workload == "batch" else run_serve)(args, R, torch)
+        metric = "rpq_queries_per_s" if args.workload == "batch" else "rpq_served_queries_per_s"
+        line = {"metric": metric, "value": r["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+                "steps": args.steps if args.workload == "batch" else 1,
+                "warmup": args.warmup if args.workload == "batch" else 1,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic", "config": {"workload": r["workload"]}}
+        line.update({k: v for k, v in r.items() if k not in ("workload", "queries_per_s")})
+        print(json.dumps(line), flush=True)
         return
     import torch
 
     ws, rank, local = dist_info()
+    dist = None
     if ws > 1:
         import torch.distributed as dist
 
@@ -605,66 +837,32 @@ def main():
     __graft_entry__.build()
     from paper_2412_10287_gb300 import rpq as R
 
-    per_template = args.per_template if args.workload == "rmat20" else min(args.per_template, 25)
-    w = workload(per_template, args.workload)
+    name = args.workload
+    per_template = per_template_for(name, args.per_template)
+    w = workload(per_template, name)
     if rank > 0:
-        w.queries = rank_queries(w.graph, args.workload, per_template, rank)
+        w.queries = rank_queries(w.graph, name, per_template, rank)
     g = w.graph
     gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
-    tuned = autotune(R, gg, g, args.workload)
+    tuned = autotune(R, gg, g, name)
     nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
     srcs = [q.source for q in w.queries]
     nq = len(srcs)
     stream = torch.cuda.current_stream()
-    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     W_words = (g.n + 63) // 64
-    if args.workload == "kb20m":
-        global PROFILE_JSON
-        PROFILE_JSON = os.path.join(ROOT, "profiles", "rpq_query_kernel_kb20m.json")
+    global PROFILE_JSON
+    PROFILE_JSON = os.path.join(ROOT, "profiles", f"rpq_query_kernel_{name}.json")
 
-    def one_step(collect):
-        res = []
-        for nfa, s in zip(nfas, srcs):
-            t0 = time.perf_counter()
-            cnt, st = R.rpq_query(gg, nfa, s, out=out, stream=stream, with_stats=True)
-            if collect:
-                res.append((time.perf_counter() - t0, st, nfa.info()[0]))
-        return res
-
-    for _ in range(args.warmup):
-        one_step(False)
-    torch.cuda.synchronize()
-
-    step_ms, recs = [], []
-    k_timed = 0
-    with ClockSampler(dev) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            if ws > 1:
-                torch.distributed.barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            k0 = R.rpq_kernel_launches()
-            e0.record(stream)
-            recs.extend(one_step(True))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            k_timed += R.rpq_kernel_launches() - k0
-            step_ms.append(e0.elapsed_time(e1))
-    clocks = clk.summary()
-    total_s = sum(step_ms) / 1000.0
+    m = measure_single(R, torch, w, gg, nfas, srcs, args.steps, args.warmup, stream,
+                       clock_dev=dev, dist=dist)
+    recs = m["recs"]
+    total_s = sum(m["step_ms"]) / 1000.0
     if ws > 1:
-        total_s = max_over_ranks(total_s, torch.distributed, "cuda")
+        total_s = max_over_ranks(total_s, dist, "cuda")
     value = ws * nq * args.steps / total_s
-
-    lat = sorted(r[0] * 1000.0 for r in recs)
-    p50 = lat[len(lat) // 2]
-    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+    p50, p99 = latency_summary(recs)
     kern_ms = [r[1]["device_ms"] for r in recs]
-    push_bytes = sum(r[1]["push_bytes"] for r in recs)
-    sweep_bytes = sum(3 * r[2] * W_words * 8 * (r[1]["levels"] + 1) for r in recs)
+    push_bytes, sweep_bytes = algorithmic_bytes(recs, W_words)
     prod_edges = sum(r[1]["product_edges"] for r in recs)
     alg_bytes_per_launch = (push_bytes + sweep_bytes) / len(recs)
     avg_launch_s = sum(kern_ms) / len(kern_ms) / 1000.0
@@ -685,8 +883,16 @@ def main():
         e2e_steps.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_steps)
     if ws > 1:
-        e2e_s = max_over_ranks(e2e_s, torch.distributed, "cuda")
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     e2e_value = ws * nq * args.steps / e2e_s
+    # per-launch DRAM traffic: the committed ncu sample's DRAM bytes per
+    # algorithmic byte, scaled to this run's algorithmic bytes per launch
+    traffic = profile_traffic(alg_bytes_per_launch)
+
+    extras = None
+    if ws == 1 and not args.no_extras:
+        gg.close()  # the R-MAT graph takes its place on the device
+        extras = run_extras(args, R, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -700,9 +906,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(w, nq, {"autotuned": tuned}),
             "p50_ms": p50, "p99_ms": p99,
-            "product_edges_per_s": ws * prod_edges / (total_s if ws == 1 else total_s),
+            "product_edges_per_s": ws * prod_edges / total_s,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profile_traffic(),
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "rpq_query_kernel",
                          "peak_kind": f"{peak_kind} copy bandwidth",
                          "algorithmic_bytes_per_launch": alg_bytes_per_launch,
@@ -710,14 +916,16 @@ def main():
                          "avg_launch_ms": avg_launch_s * 1000.0},
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": k_timed,
-            "clocks": clocks,
+            "gpu_launches": m["launches"],
+            "clocks": m["clocks"],
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if extras:
+            line["extras"] = extras
         print(json.dumps(line), flush=True)
     if ws > 1:
-        torch.distributed.destroy_process_group()
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

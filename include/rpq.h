@@ -226,10 +226,18 @@ rpq_status rpq_query_bitset(const rpq_graph *g, const rpq_nfa *nfa, int32_t sour
                             int32_t max_levels, uint64_t *out_bits, int64_t *out_count,
                             rpq_stats *stats, void *stream);
 
-/* Many single-source queries in one launch: query i is (nfas[i], sources[i]).
- * Queries are packed as bit lanes of uint64 words (64 queries per lane word),
- * so one pass over G^a per level serves all of them (multi-source BFS,
- * section 6).  Results are concatenated: query i's vertices (ascending) are
+/* Many single-source queries in one call: query i is (nfas[i], sources[i]).
+ * Two engines, chosen per call:
+ *   - bit lanes, when every query shares one automaton and there are at
+ *     least 16 of them: up to 256 queries packed as bits of uint64 lane
+ *     words, so one pass over G^a per level serves all of them (multi-source
+ *     BFS, named as future work in section 6);
+ *   - otherwise concurrent query slots: the single-query kernel of rpq_query
+ *     runs the queries in turn on several streams at once, each kernel on a
+ *     share of the SMs.
+ * The environment variable RPQ_BATCH_ENGINE (= "lanes" or "slots") overrides
+ * the choice.  Answers never depend on the engine.  Results are
+ * concatenated: query i's vertices (ascending) are
  * out_vertices[out_offsets[i] .. out_offsets[i+1]).  out_offsets (n+1 int64)
  * is always filled; RPQ_ERR_CAPACITY when the total exceeds `capacity`.
  * `stats` may be NULL or an array of n entries.  Automata may have up to 64

@@ -1017,7 +1017,11 @@ rpq_status slot_batch(rpq_graph *g, const Automaton *const *autos, const int32_t
     auto worker = [&]() {
         cudaSetDevice(g->device);
         cudaStream_t s2 = nullptr;
-        if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+        const cudaError_t ce = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(msg_mu);
+            if (msg.empty())
+                msg = std::string("cudaStreamCreateWithFlags (slot stream): ") + cudaGetErrorString(ce);
             first_err = (int)RPQ_ERR_CUDA;
             return;
         }

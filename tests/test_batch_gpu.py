@@ -51,7 +51,7 @@ def test_batch_shared_automaton_many_sources():
     nfa = R.rpq_nfa_compile("(0|^1)*/2", 4)
     got = R.rpq_query_batch(gg, [nfa] * 200, srcs)
     on = oracle_compile("(0|^1)*/2", 4)
-    for i in range(0, 200, 7):
+    for i in range(200):
         assert got[i].tolist() == og.ssr(on, srcs[i])["answer"].tolist(), i
 
 

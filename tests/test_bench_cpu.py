@@ -118,3 +118,43 @@ def test_clock_summary_median_max_and_reasons(tmp_path):
 def test_clock_summary_without_samples(tmp_path):
     out = clock_rows(tmp_path, [])
     assert out == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+
+def test_write_profile_sample_ratio_scales_traffic(tmp_path, monkeypatch):
+    """A capture of a few sample launches stores DRAM bytes per algorithmic
+    byte; the traffic of a run's mean launch is that ratio times the run's
+    algorithmic bytes per launch."""
+    k = "rpq::<unnamed>::rpq_query_kernel(rpq::<unnamed>::KParams)"
+    rows = [("7", k, "dram__bytes_read.sum", "byte", "3,000"),
+            ("7", k, "dram__bytes_write.sum", "byte", "1,000"),
+            ("9", k, "dram__bytes_read.sum", "byte", "5,000"),
+            ("9", k, "dram__bytes_write.sum", "byte", "1,000")]
+    src = tmp_path / "ncu.csv"
+    src.write_text(ncu_csv(rows))
+    sj = tmp_path / "sample.json"
+    sj.write_text(json.dumps({"algorithmic_bytes": [2000, 3000], "push_bytes": [500, 500],
+                              "sample": "two launches"}))
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    bench.write_profile(str(src), "unit", str(sj))
+    out = json.loads((tmp_path / "profiles" / "rpq_query_kernel_unit.json").read_text())
+    assert out["dram_per_algorithmic_byte"] == pytest.approx(10000 / 5000)
+    assert out["dram_per_push_byte"] == pytest.approx(10.0)
+    monkeypatch.setattr(bench, "PROFILE_JSON", str(tmp_path / "profiles" / "rpq_query_kernel_unit.json"))
+    assert bench.profile_traffic(1e6) == pytest.approx(2e6)
+    assert bench.profile_traffic() == pytest.approx(5000.0)  # the sample's own mean
+    sj.write_text(json.dumps({"algorithmic_bytes": [2000], "push_bytes": [500]}))
+    with pytest.raises(SystemExit):  # launches and sample queries must pair up
+        bench.write_profile(str(src), "unit", str(sj))
+
+
+def test_oracle_sample_is_bounded_and_counts_what_ran():
+    from paper_2412_10287_gb300 import workloads as W
+
+    g = W.rmat_graph(10, 6000, 8, seed=5)
+    qs = W.make_queries(g, W.TEMPLATES_SMALL, 5, seed=1, zipf_s=1.0)
+    w = W.Workload("rmat10", g, qs)
+    r = bench.oracle_sample(w, 0.0, max_threads=2)  # no time: one round of submissions
+    assert 1 <= r["queries"] <= 2 and r["cores"] == 2 and r["kind"] == "oracle"
+    r = bench.oracle_sample(w, 30.0, max_threads=2)
+    assert r["queries"] == len(qs) and r["value"] == pytest.approx(r["queries"] / r["wall_s"])

@@ -87,11 +87,19 @@ def test_compiled_dfa_is_minimal_on_known_cases():
     assert R.rpq_nfa_compile("(0|1)*/2", 3).info()[0] == 2
     assert R.rpq_nfa_compile("0/1/2/0/1", 3).info()[0] == 6
     assert R.rpq_nfa_compile("(0/1)*", 3).info()[0] == 2
-    # empty language: one non-final state, no transitions
-    S, T, _ = R.rpq_nfa_compile("0/^0/(1|2)", 3).info()
-    assert S >= 1
+    # a finite language of two words, 0.0^-.1 and 0.0^-.2: a chain of three
+    # states and one final state reached by either last symbol
+    d = R.rpq_nfa_compile("0/^0/(1|2)", 3)
+    S, T, _ = d.info()
+    assert (S, T) == (4, 4)
+    e = d.export()
+    assert e["starts"] == [0] and e["finals"] == [3]
+    accepted = [w for k in range(5) for w in itertools.product(range(6), repeat=k) if d.accepts(w)]
+    assert accepted == [(0, 3, 1), (0, 3, 2)]
+    # 0?: the empty word and "0"; both states final
     e = R.rpq_nfa_compile("0?", 1).export()
-    assert e["finals"] == [0, 1] or 0 in e["finals"]
+    assert e["n_states"] == 2 and e["finals"] == [0, 1]
+    assert e["from"].tolist() == [0] and e["label"].tolist() == [0] and e["to"].tolist() == [1]
 
 
 def test_reverse_automaton_language():

@@ -40,18 +40,29 @@ def test_kb_scaled_parity():
 
 @pytest.mark.slow
 def test_kb20m_full_size():
-    """Full size: three queries against the oracle, and properties that hold
-    at any size (P_k grows with k; union of languages = union of answers)."""
+    """Full size (20M vertices, 200M edges, 500 labels): the first query of
+    every benchmark template -- inverse labels included -- against the
+    oracle, and properties that hold at any size (P_k grows with k; union of
+    languages = union of answers)."""
+    import concurrent.futures as cf
+    import os
+
     w = W.config3(per_template=1)
     g = w.graph
+    assert sorted({q.template for q in w.queries}) == sorted(W.TEMPLATES_KB)
     gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
-    picks = [q for q in w.queries if not q.regex.startswith("(")][:3]
     og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
-    for q in picks:
-        exp = og.ssr(oracle_compile(q.regex, g.n_labels), q.source)["answer"]
-        got = R.rpq_query(gg, R.rpq_nfa_compile(q.regex, g.n_labels), q.source)
-        assert got.tolist() == exp.tolist(), q
+
+    def oracle_answer(q):
+        return og.ssr(oracle_compile(q.regex, g.n_labels), q.source)["answer"]
+
+    with cf.ThreadPoolExecutor(max_workers=len(os.sched_getaffinity(0))) as ex:
+        exp = list(ex.map(oracle_answer, w.queries))
     og.close()
+    assert any(q.template.count("^") for q in w.queries)
+    for q, e in zip(w.queries, exp):
+        got = R.rpq_query(gg, R.rpq_nfa_compile(q.regex, g.n_labels), q.source)
+        assert got.tolist() == e.tolist(), q
     for q in w.queries[:4]:
         nfa = R.rpq_nfa_compile(q.regex, g.n_labels)
         prev = set()
