@@ -10,6 +10,14 @@ Functions and the passages they follow (paper arXiv:2412.10287):
 * :func:`ssr` -- the pair BFS of ``rpq_oracle.c``: the single-source
   reachability answer of section 2 computed level by level as in
   Algorithm 1 (section 4), one level per word length (appendix invariant).
+* :meth:`OracleGraph.query` -- the same search from a set of sources V_s
+  (the 2-RPQ of section 2 takes a set of starting vertices), optionally with
+  the level of first reach of every answer vertex: the length of the
+  shortest accepted word labelling a 2-path from a source to it.
+* :meth:`OracleGraph.sdr` -- single-destination reachability (section 2) by its own
+  definition: the vertices u whose single-source answer contains v_f.
+* :func:`check_witness` -- whether a given vertex/symbol sequence is a 2-path
+  from a source that spells an accepted word (a checker for path outputs).
 * :func:`alg1_dense` -- Algorithm 1 written with dense Boolean matrices in the
   paper's own notation: M <- (OR_a (N^a)^T x M x G^a)<not P>, P <- P + M,
   until M = 0; result F x P (section 3 operations, section 4 listing).
@@ -67,6 +75,9 @@ def _lib():
         L.oracle_ssr_graph.restype = ctypes.c_int
         L.oracle_ssr_graph.argtypes = [p, i32, i32, p, p, p, i32, p, i32, p, i32, i32,
                                        p, p, p, i32, p]
+        L.oracle_query_graph.restype = ctypes.c_int
+        L.oracle_query_graph.argtypes = [p, i32, i32, p, p, p, i32, p, i32, p, i32, p, i32,
+                                         p, p, p, i32, p, p]
         _LIB = L
     return _LIB
 
@@ -103,23 +114,33 @@ class OracleGraph:
         self.close()
 
     def ssr(self, nfa: Nfa, source: int, max_levels: int = 0, want_visited: bool = False,
-            level_cap: int = 0):
+            level_cap: int = 0, want_first_level: bool = False):
         """Run one query.  Returns a dict with ``answer`` (sorted int32 vertex
-        ids), ``counters`` (dict), optionally ``visited`` (S x n bool) and
-        ``level_sizes`` (pairs per level)."""
+        ids), ``counters`` (dict), optionally ``visited`` (S x n bool),
+        ``level_sizes`` (pairs per level) and ``first_level`` (n int32: level
+        of first reach of each answer vertex, -1 elsewhere)."""
+        return self.query(nfa, [int(source)], max_levels, want_visited, level_cap,
+                          want_first_level)
+
+    def query(self, nfa: Nfa, sources, max_levels: int = 0, want_visited: bool = False,
+              level_cap: int = 0, want_first_level: bool = False):
+        """The query from the set of sources ``sources`` (level 0 = Q_S x
+        V_s); same outputs as :meth:`ssr`."""
         S, tf, tl, tt, st, fi = nfa.arrays()
         i32 = lambda x: np.ascontiguousarray(np.asarray(x, dtype=np.int32).reshape(-1))
         tf, tl, tt, st, fi = i32(tf), i32(tl), i32(tt), i32(st), i32(fi)
+        srcs = i32(sources)
         ans = np.zeros(self.n, np.uint8)
         vis = np.zeros((S, self.n), np.uint8) if want_visited else None
         lv = np.zeros(level_cap, np.int64) if level_cap > 0 else None
+        fl = np.zeros(self.n, np.int32) if want_first_level else None
         cnt = np.zeros(len(COUNTER_NAMES), np.int64)
-        rc = _lib().oracle_ssr_graph(
+        rc = _lib().oracle_query_graph(
             self._h, S, tf.size, _ptr(tf), _ptr(tl), _ptr(tt), st.size, _ptr(st),
-            fi.size, _ptr(fi), int(source), int(max_levels), _ptr(ans), _ptr(vis), _ptr(lv),
-            int(level_cap), _ptr(cnt))
+            fi.size, _ptr(fi), srcs.size, _ptr(srcs), int(max_levels), _ptr(ans), _ptr(vis),
+            _ptr(lv), int(level_cap), _ptr(cnt), _ptr(fl))
         if rc != 0:
-            raise ValueError(f"oracle_ssr_graph failed with status {rc}")
+            raise ValueError(f"oracle_query_graph failed with status {rc}")
         out = {
             "answer": np.flatnonzero(ans).astype(np.int32),
             "counters": dict(zip(COUNTER_NAMES, (int(x) for x in cnt))),
@@ -128,7 +149,18 @@ class OracleGraph:
             out["visited"] = vis.astype(bool)
         if lv is not None:
             out["level_sizes"] = lv
+        if fl is not None:
+            out["first_level"] = fl
         return out
+
+    def sdr(self, nfa: Nfa, target: int, candidates=None):
+        """Single-destination reachability (section 2): the sorted vertices u
+        such that some 2-path from u to ``target`` spells an accepted word,
+        i.e. whose single-source answer holds ``target`` -- the definition,
+        one single-source query per candidate u (all vertices by default)."""
+        cand = range(self.n) if candidates is None else candidates
+        hit = [int(u) for u in cand if target in set(self.ssr(nfa, int(u))["answer"].tolist())]
+        return np.array(sorted(hit), dtype=np.int32)
 
 
 def ssr(n, n_labels, src, dst, lab, nfa: Nfa, source: int, max_levels: int = 0, **kw):
@@ -222,7 +254,9 @@ def brute_force_levels(n, L, src, dst, lab, source, accepts, max_len: int):
     from v to u), and the union of reach(w) over the accepted words.  Words
     are enumerated depth-first; a word whose reach set is empty is not
     extended, since no 2-path spells any of its extensions.  ``accepts`` is
-    any word-membership predicate."""
+    any word-membership predicate.  ``source`` may also be a collection of
+    vertices (a set of sources V_s): a 2-path may then start at any of
+    them."""
     edges = {s: [] for s in range(2 * L)}
     for u, v, a in zip(map(int, src), map(int, dst), map(int, lab)):
         edges[a].append((u, v))
@@ -239,7 +273,8 @@ def brute_force_levels(n, L, src, dst, lab, source, accepts, max_len: int):
             if nxt:
                 dfs(word + (s,), nxt)
 
-    dfs((), {int(source)})
+    start = {int(source)} if np.ndim(source) == 0 else {int(x) for x in source}
+    dfs((), start)
     out, acc = [], set()
     for k in range(max_len + 1):
         acc |= per_len[k]
@@ -250,3 +285,42 @@ def brute_force_levels(n, L, src, dst, lab, source, accepts, max_len: int):
 def brute_force(n, L, src, dst, lab, source, accepts, max_len: int):
     """Answer restricted to words of length <= max_len (see brute_force_levels)."""
     return brute_force_levels(n, L, src, dst, lab, source, accepts, max_len)[-1]
+
+
+def first_levels_from(levels_answers, n):
+    """Level of first reach per vertex from per-bound answers (answers[k] =
+    the answer restricted to words of length <= k): the smallest k whose
+    answer holds v, -1 if none does."""
+    out = np.full(n, -1, np.int32)
+    for k in range(len(levels_answers) - 1, -1, -1):
+        out[np.asarray(levels_answers[k], dtype=np.int64)] = k
+    return out
+
+
+def check_witness(n, L, src, dst, lab, accepts, sources, target, vertices, symbols):
+    """Whether vertices[0..k] / symbols[0..k-1] is a witness of ``target``:
+    vertices[0] is a source, vertices[-1] is the target, step i walks an
+    edge vertices[i] -a-> vertices[i+1] of label a = symbols[i] (a < L) or,
+    for a >= L, an edge vertices[i+1] -(a-L)-> vertices[i] backwards (the
+    2-path of section 2), and the word of symbols is accepted.  Returns
+    (ok, reason)."""
+    vertices = [int(x) for x in vertices]
+    symbols = [int(x) for x in symbols]
+    if len(vertices) != len(symbols) + 1:
+        return False, "vertices must be one longer than symbols"
+    if vertices[0] not in {int(x) for x in np.atleast_1d(sources)}:
+        return False, "does not start at a source"
+    if vertices[-1] != int(target):
+        return False, "does not end at the target"
+    edges = set(zip(map(int, src), map(int, dst), map(int, lab)))
+    for i, a in enumerate(symbols):
+        u, v = vertices[i], vertices[i + 1]
+        if not 0 <= a < 2 * L:
+            return False, f"symbol {a} out of range"
+        if a < L and (u, v, a) not in edges:
+            return False, f"step {i}: no edge {u} -{a}-> {v}"
+        if a >= L and (v, u, a - L) not in edges:
+            return False, f"step {i}: no edge {v} -{a - L}-> {u} to walk backwards"
+    if not accepts(tuple(symbols)):
+        return False, "word not accepted"
+    return True, ""

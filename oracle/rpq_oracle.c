@@ -28,6 +28,17 @@
  *
  * Labels: a in [0, L) is a forward label, a + L stands for a^-.
  *
+ * Two more outputs, from the same search:
+ *   - a set of sources V_s (the 2-RPQ of section 2 takes a set of starting
+ *     vertices): level 0 is then Q_S x V_s, and the answer is the set of
+ *     vertices reached from some source, i.e. the union of the answers of
+ *     the single sources;
+ *   - the level of first reach of every answer vertex v: the smallest k such
+ *     that (q_f, v) is in level k for some final q_f.  By the invariant (**)
+ *     this is the length of the shortest accepted word that labels a 2-path
+ *     from a source to v (a shortest-path output in the sense of the
+ *     semiring variants the paper's conclusion lists).
+ *
  * Parity pins: brute-force path enumeration, closed forms and metamorphic
  * identities in tests/test_oracle.py.
  */
@@ -129,35 +140,46 @@ EXPORT void oracle_graph_free(void *hp) {
 }
 
 /*
- * Single-source 2-RPQ by pair BFS on a graph from oracle_graph_new.
+ * 2-RPQ from a set of sources by pair BFS on a graph from oracle_graph_new.
  *   automaton: S states, T transitions (t_from, t_label, t_to), t_label in [0, 2L);
  *          start and final states as lists.
- *   source: v_s.  max_levels: 0 = until the frontier is empty.
+ *   sources: n_sources vertex ids (repeats allowed), the set V_s.
+ *   max_levels: 0 = until the frontier is empty.
  *   out_answer: n bytes, 1 where v is in the answer.
  *   out_visited: S*n bytes (row q, column v) or NULL.
  *   out_level_sizes: number of pairs in each level 0,1,2,... (up to level_cap entries) or NULL.
  *   counters: ORC_NCOUNTERS int64 or NULL.
+ *   out_first_level: n int32 or NULL: level of first reach of each answer
+ *          vertex (see above), -1 for vertices outside the answer.
  */
-EXPORT int oracle_ssr_graph(const void *hp, int32_t S, int32_t T, const int32_t *t_from,
-                            const int32_t *t_label, const int32_t *t_to, int32_t n_start,
-                            const int32_t *starts, int32_t n_final, const int32_t *finals,
-                            int32_t source, int32_t max_levels, uint8_t *out_answer,
-                            uint8_t *out_visited, int64_t *out_level_sizes, int32_t level_cap,
-                            int64_t *counters) {
+EXPORT int oracle_query_graph(const void *hp, int32_t S, int32_t T, const int32_t *t_from,
+                              const int32_t *t_label, const int32_t *t_to, int32_t n_start,
+                              const int32_t *starts, int32_t n_final, const int32_t *finals,
+                              int32_t n_sources, const int32_t *sources, int32_t max_levels,
+                              uint8_t *out_answer, uint8_t *out_visited,
+                              int64_t *out_level_sizes, int32_t level_cap, int64_t *counters,
+                              int32_t *out_first_level) {
     const oracle_graph_t *h = (const oracle_graph_t *)hp;
     if (!h) return ORC_EINVAL;
     const int32_t n = h->n, L = h->L;
-    if (S <= 0 || T < 0 || source < 0 || source >= n || max_levels < 0) return ORC_EINVAL;
+    if (S <= 0 || T < 0 || n_sources < 0 || (n_sources > 0 && !sources) || max_levels < 0)
+        return ORC_EINVAL;
+    for (int32_t i = 0; i < n_sources; i++)
+        if (sources[i] < 0 || sources[i] >= n) return ORC_EINVAL;
     for (int32_t t = 0; t < T; t++)
         if (t_from[t] < 0 || t_from[t] >= S || t_to[t] < 0 || t_to[t] >= S || t_label[t] < 0 ||
             t_label[t] >= 2 * L)
             return ORC_EINVAL;
+    for (int32_t i = 0; i < n_final; i++)
+        if (finals[i] < 0 || finals[i] >= S) return ORC_EINVAL;
 
     int rc = ORC_OK;
     const adjlist_t g = h->g;
     int64_t *d_off = NULL;   /* delta(q, a) as lists: index q*2L + a */
     int32_t *d_to = NULL;
     uint8_t *vis = NULL;
+    uint8_t *is_final = NULL;
+    int32_t *first = NULL;   /* level of first reach in a final state, per vertex */
     int32_t *cur = NULL, *nxt = NULL; /* frontier pairs, (q, v) interleaved */
     int64_t *deg = NULL;      /* deg_a(v) per (v, a) is computed on the fly */
     int64_t cnt[ORC_NCOUNTERS] = {0};
@@ -179,19 +201,27 @@ EXPORT int oracle_ssr_graph(const void *hp, int32_t S, int32_t T, const int32_t 
 
     int64_t npairs = (int64_t)S * n;
     vis = (uint8_t *)calloc((size_t)npairs, 1);
+    is_final = (uint8_t *)calloc((size_t)S, 1);
+    first = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     cur = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)npairs);
     nxt = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)npairs);
     deg = (int64_t *)calloc((size_t)2 * L, sizeof(int64_t));
-    if (!vis || !cur || !nxt || !deg) { rc = ORC_ENOMEM; goto done; }
+    if (!vis || !is_final || !first || !cur || !nxt || !deg) { rc = ORC_ENOMEM; goto done; }
+    for (int32_t i = 0; i < n_final; i++) is_final[finals[i]] = 1;
+    for (int32_t v = 0; v < n; v++) first[v] = -1;
 
-    /* level 0: Q_S x {v_s} */
+    /* level 0: Q_S x V_s */
     int64_t ncur = 0;
-    for (int32_t i = 0; i < n_start; i++) {
-        int32_t q = starts[i];
-        if (q < 0 || q >= S) { rc = ORC_EINVAL; goto done; }
-        if (!vis[(int64_t)q * n + source]) {
-            vis[(int64_t)q * n + source] = 1;
-            cur[2 * ncur] = q; cur[2 * ncur + 1] = source; ncur++;
+    for (int32_t k = 0; k < n_sources; k++) {
+        const int32_t v = sources[k];
+        for (int32_t i = 0; i < n_start; i++) {
+            int32_t q = starts[i];
+            if (q < 0 || q >= S) { rc = ORC_EINVAL; goto done; }
+            if (!vis[(int64_t)q * n + v]) {
+                vis[(int64_t)q * n + v] = 1;
+                cur[2 * ncur] = q; cur[2 * ncur + 1] = v; ncur++;
+                if (is_final[q] && first[v] < 0) first[v] = 0;
+            }
         }
     }
     cnt[ORC_C_VISITED] = ncur;
@@ -215,6 +245,9 @@ EXPORT int oracle_ssr_graph(const void *hp, int32_t S, int32_t T, const int32_t 
                     if (!vis[idx]) {
                         vis[idx] = 1;
                         nxt[2 * nnext] = q2; nxt[2 * nnext + 1] = w; nnext++;
+                        /* levels are visited in increasing order: the first
+                         * final pair of w found is at its smallest level */
+                        if (is_final[q2] && first[w] < 0) first[w] = level + 1;
                     }
                 }
             }
@@ -234,17 +267,30 @@ EXPORT int oracle_ssr_graph(const void *hp, int32_t S, int32_t T, const int32_t 
     memset(out_answer, 0, (size_t)n);
     for (int32_t i = 0; i < n_final; i++) {
         int32_t q = finals[i];
-        if (q < 0 || q >= S) { rc = ORC_EINVAL; goto done; }
         for (int32_t v = 0; v < n; v++)
             if (vis[(int64_t)q * n + v]) out_answer[v] = 1;
     }
     for (int32_t v = 0; v < n; v++) cnt[ORC_C_ANSWER] += out_answer[v];
     if (out_visited) memcpy(out_visited, vis, (size_t)npairs);
     if (counters) memcpy(counters, cnt, sizeof(cnt));
+    if (out_first_level) memcpy(out_first_level, first, sizeof(int32_t) * (size_t)n);
 
 done:
-    free(d_off); free(d_to); free(vis); free(cur); free(nxt); free(deg);
+    free(d_off); free(d_to); free(vis); free(is_final); free(first); free(cur); free(nxt);
+    free(deg);
     return rc;
+}
+
+/* The single-source form: V_s = {source}. */
+EXPORT int oracle_ssr_graph(const void *hp, int32_t S, int32_t T, const int32_t *t_from,
+                            const int32_t *t_label, const int32_t *t_to, int32_t n_start,
+                            const int32_t *starts, int32_t n_final, const int32_t *finals,
+                            int32_t source, int32_t max_levels, uint8_t *out_answer,
+                            uint8_t *out_visited, int64_t *out_level_sizes, int32_t level_cap,
+                            int64_t *counters) {
+    return oracle_query_graph(hp, S, T, t_from, t_label, t_to, n_start, starts, n_final, finals,
+                              1, &source, max_levels, out_answer, out_visited, out_level_sizes,
+                              level_cap, counters, NULL);
 }
 
 /* One-shot form: builds the adjacency lists, runs one query, frees them. */

@@ -377,3 +377,112 @@ def test_golden_config1():
     r = answer(g, compile_regex(q.regex, g.n_labels), q.source)
     assert r["answer"].tolist() == fx["answer"]
     assert r["counters"] == fx["counters"]
+
+
+# ------------------------------------------------------ sets of sources ----
+# The 2-RPQ of section 2 takes a set of starting vertices V_s; level 0 is
+# then Q_S x V_s.
+
+@pytest.mark.parametrize("seed", range(40))
+def test_source_set_vs_bruteforce(seed):
+    """Brute force from the definition with 2-paths starting anywhere in V_s
+    (repeats allowed in the list), per word-length bound k."""
+    g = W.tiny_graph(seed + 900)
+    S, trans, starts, finals = W.tiny_automaton(seed + 1900, g.n_labels)
+    nfa = nfa_from_lists(S, trans, starts, finals, g.n_labels)
+    r = W.below(seed, 12, 4, 1 << 20)
+    srcs = [int(x % g.n) for x in r[: 1 + seed % 4]]
+    og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+    K = 5
+    bf = O.brute_force_levels(g.n, g.n_labels, g.src, g.dst, g.lab, srcs, nfa.accepts, K)
+    for k in range(1, K + 1):
+        assert as_set(og.query(nfa, srcs, k)["answer"]) == as_set(bf[k]), (k, srcs)
+    og.close()
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_source_set_is_union_of_single_sources(seed):
+    """Ans(V_s) = union over v in V_s of Ans(v), at every level bound."""
+    g = W.rmat_graph(7, 500, 3, seed=seed + 60)
+    text, _, _ = W.random_regex(seed + 61, 3, 3)
+    nfa = compile_regex(text, 3)
+    og = O.OracleGraph(g.n, 3, g.src, g.dst, g.lab)
+    srcs = W.below(seed, 13, 5, g.n).tolist()
+    for k in (0, 1, 3):
+        union = set()
+        for s in srcs:
+            union |= as_set(og.ssr(nfa, s, k)["answer"])
+        assert as_set(og.query(nfa, srcs, k)["answer"]) == union, (text, k)
+    assert og.query(nfa, [], 0)["answer"].size == 0  # no source: nothing is reached
+    og.close()
+
+
+# ------------------------------------------------- level of first reach ----
+# The smallest k such that v is in the answer restricted to words of length
+# <= k: the length of a shortest accepted word labelling a 2-path to v.
+
+@pytest.mark.parametrize("seed", range(40))
+def test_first_level_vs_bruteforce(seed):
+    g = W.tiny_graph(seed + 1300)
+    S, trans, starts, finals = W.tiny_automaton(seed + 2300, g.n_labels)
+    nfa = nfa_from_lists(S, trans, starts, finals, g.n_labels)
+    srcs = [seed % g.n] if seed % 2 else [seed % g.n, (seed * 5 + 1) % g.n]
+    og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+    K = 5
+    bf = O.brute_force_levels(g.n, g.n_labels, g.src, g.dst, g.lab, srcs, nfa.accepts, K)
+    exp = O.first_levels_from(bf, g.n)
+    got = og.query(nfa, srcs, 0, want_first_level=True)
+    fl = got["first_level"]
+    for v in range(g.n):
+        if exp[v] >= 0:
+            assert fl[v] == exp[v], (v, srcs, trans, starts, finals)
+        else:  # not reached within K symbols: later or never
+            assert fl[v] == -1 or fl[v] > K, (v, fl[v])
+    assert as_set(np.flatnonzero(fl >= 0)) == as_set(got["answer"])
+    og.close()
+
+
+def test_first_level_closed_forms():
+    # a* on a chain 0 -> 1 -> ... -> 9 from 3: vertex 3 + i first at level i
+    m, s = 10, 3
+    src = np.arange(m - 1, dtype=np.int32)
+    dst = src + 1
+    lab = np.zeros(m - 1, np.int32)
+    og = O.OracleGraph(m, 1, src, dst, lab)
+    fl = og.ssr(compile_regex("0*", 1), s, want_first_level=True)["first_level"]
+    assert fl.tolist() == [-1] * s + list(range(m - s))
+    # ^0* from 6 walks the chain backwards
+    fl = og.ssr(compile_regex("^0*", 1), 6, want_first_level=True)["first_level"]
+    assert fl.tolist() == [6, 5, 4, 3, 2, 1, 0, -1, -1, -1]
+    og.close()
+    # a* on a directed cycle of length 7 from 2: (v - 2) mod 7
+    n = 7
+    src = np.arange(n, dtype=np.int32)
+    dst = (src + 1) % n
+    og = O.OracleGraph(n, 1, src, dst, np.zeros(n, np.int32))
+    fl = og.ssr(compile_regex("0*", 1), 2, want_first_level=True)["first_level"]
+    assert fl.tolist() == [(v - 2) % n for v in range(n)]
+    # (0/0)* on the cycle: even word lengths only, so v is first reached at
+    # the smallest even length congruent to (v - 2) mod 7
+    fl = og.ssr(compile_regex("(0/0)*", 1), 2, want_first_level=True)["first_level"]
+    assert fl.tolist() == [d if d % 2 == 0 else d + 7 for d in ((v - 2) % n for v in range(n))]
+    # from the set {0, 4}: the nearer source decides
+    fl = og.query(compile_regex("0*", 1), [0, 4], want_first_level=True)["first_level"]
+    assert fl.tolist() == [min(v % n, (v - 4) % n) for v in range(n)]
+    og.close()
+
+
+# ------------------------------------------------------------ witnesses ----
+
+def test_check_witness_accepts_valid_and_rejects_broken_paths():
+    # edges 0 -a-> 1 -b-> 2, 3 -a-> 2 (a = 0, b = 1, L = 2)
+    src, dst, lab = [0, 1, 3], [1, 2, 2], [0, 1, 0]
+    acc = compile_regex("0/1/^0", 2).accepts
+    ok = lambda vs, ws, t=3, s=(0,): O.check_witness(4, 2, src, dst, lab, acc, s, t, vs, ws)[0]
+    assert ok([0, 1, 2, 3], [0, 1, 2])            # a, b, then a backwards from 2 to 3
+    assert not ok([0, 1, 2, 3], [0, 1, 0])        # 2 -a-> 3 is not an edge
+    assert not ok([1, 2, 3], [1, 2], s=(0,))      # does not start at the source
+    assert ok([1, 2, 3], [1, 2], s=(0, 1)) is False  # starts at a source, word not accepted
+    assert not ok([0, 1, 2], [0, 1], t=2)         # word a.b not accepted
+    assert not ok([0, 1, 2, 3], [0, 1])           # lengths do not pair up
+    assert not ok([0, 1, 2, 3], [0, 1, 2], t=2)   # does not end at the target
