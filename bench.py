@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--per-template", type=int, default=100)
+    ap.add_argument("--per-template", type=int, default=None,
+                    help="sources per template (default: 25 on kb20m, 100 on rmat20)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")

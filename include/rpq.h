@@ -226,6 +226,65 @@ rpq_status rpq_query_bitset(const rpq_graph *g, const rpq_nfa *nfa, int32_t sour
                             int32_t max_levels, uint64_t *out_bits, int64_t *out_count,
                             rpq_stats *stats, void *stream);
 
+/* 2-RPQ from a set of sources (section 2: a 2-RPQ takes a set V_s of
+ * starting vertices): the vertices v such that some 2-path from some vertex
+ * of V_s to v spells a word accepted by `nfa`, in ascending order -- the
+ * union of the single-source answers of the vertices of V_s.  One traversal:
+ * level 0 of Algorithm 1 is Q_S x V_s.
+ *   sources: host memory, n_sources vertex ids in [0, n) (repeats allowed);
+ *     n_sources = 0 gives the empty answer.
+ *   Other arguments, outputs (rpq_last_answer included) and errors as
+ *   rpq_query. */
+rpq_status rpq_query_multi(const rpq_graph *g, const rpq_nfa *nfa, int32_t n_sources,
+                           const int32_t *sources, int32_t max_levels, int32_t *out_vertices,
+                           int64_t capacity, int64_t *out_count, rpq_stats *stats, void *stream);
+
+/* Single-destination reachability (section 2): the vertices u such that
+ * some 2-path from u to `target` spells a word accepted by `nfa`, in
+ * ascending order.  Computed as section 4 states, SDR(Q) = SSR(Q^-): the
+ * single-source query of the reversed automaton N^- (transitions reversed
+ * with inverted labels, start and final sets swapped) from `target`.
+ *   max_levels: 0 = unbounded; k > 0 = paths of length <= k.
+ *   Outputs (rpq_last_answer included) and errors as rpq_query. */
+rpq_status rpq_query_sdr(const rpq_graph *g, const rpq_nfa *nfa, int32_t target,
+                         int32_t max_levels, int32_t *out_vertices, int64_t capacity,
+                         int64_t *out_count, rpq_stats *stats, void *stream);
+
+/* The answer of the query from `sources` (as rpq_query_multi) with each
+ * vertex's level of first reach: the smallest k such that a pair (q_f, v),
+ * q_f final, is discovered at level k, which is the length of the shortest
+ * accepted word that labels a 2-path from a source to v (section 4: level k
+ * holds the pairs first reached by words of length k; one of the path
+ * outputs the conclusion, section 6, lists).
+ *   out_vertices, out_levels: capacity entries each, both host or both
+ *     device memory; entry i of out_levels belongs to out_vertices[i].
+ *   Errors as rpq_query_multi; RPQ_ERR_CAPACITY with *out_count set. */
+rpq_status rpq_query_levels(const rpq_graph *g, const rpq_nfa *nfa, int32_t n_sources,
+                            const int32_t *sources, int32_t max_levels, int32_t *out_vertices,
+                            int32_t *out_levels, int64_t capacity, int64_t *out_count,
+                            void *stream);
+
+/* A shortest witness for `target` (single path output, section 6): a 2-path
+ * from a vertex of `sources` to `target` whose word is accepted by `nfa` and
+ * has the length of the target's level of first reach.  Built on the device
+ * backwards from the target, one level at a time, through the discovery
+ * level of every visited pair; where several predecessors qualify, the one
+ * earliest in the automaton's transition order and then in the adjacency
+ * row is taken.
+ *   path_vertices: *out_length + 1 vertices, path_vertices[0] a source,
+ *     the last one `target`; path_symbols: *out_length symbols, symbol i
+ *     leads from path_vertices[i] to path_vertices[i+1]: a < L walks an edge
+ *     of label a forwards, a >= L an edge of label a - L backwards.  Both
+ *     host memory of `capacity` entries.
+ *   *out_length = -1 (and RPQ_OK) when the target is not in the answer.
+ *   Errors: RPQ_ERR_INVALID (empty source set, target or a source out of
+ *   range), RPQ_ERR_CAPACITY (with *out_length set) when the path does not
+ *   fit, and those of rpq_query. */
+rpq_status rpq_query_witness(const rpq_graph *g, const rpq_nfa *nfa, int32_t n_sources,
+                             const int32_t *sources, int32_t target, int32_t max_levels,
+                             int32_t *path_vertices, int32_t *path_symbols, int32_t capacity,
+                             int32_t *out_length, void *stream);
+
 /* Many single-source queries in one call: query i is (nfas[i], sources[i]).
  * Two engines, chosen per call:
  *   - bit lanes, when every query shares one automaton and there are at
@@ -254,7 +313,8 @@ typedef struct rpq_serve_config {
                                 (0 = 12, at most 64), bit lanes for engine 1 (0 = 256) */
     int32_t max_states;      /* state slots per lane, engine 1 (0 = 16) */
     int32_t queue_capacity;  /* submitted-but-not-admitted queries (0 = 65536) */
-    int64_t memory_budget;   /* bytes of device state the server may hold (0 = no limit) */
+    int64_t memory_budget;   /* bytes of device state the admitted queries may hold at once
+                                (0 = no limit); see rpq_serve_create */
     int32_t max_levels;      /* per-query level cap (0 = none) */
     int32_t engine;          /* 0: concurrent query slots -- each admitted query runs the
                                 single-query kernel on its own stream and 1/slots of the SMs;
@@ -264,12 +324,16 @@ typedef struct rpq_serve_config {
 
 typedef struct rpq_serve_stats {
     int64_t submitted, admitted, completed, rejected;
-    int64_t level_steps;     /* device level steps run */
+    int64_t level_steps;     /* level expansions run on the device: engine 0, the levels each
+                                completed query expanded; engine 1, lane steps (one level of
+                                every active lane each) */
     double p50_ms, p99_ms;   /* submit -> completion latency over completed queries */
     double mean_ms;
     double elapsed_s;        /* since the first submission */
     double qps;              /* completed / elapsed_s */
-} rpq_serve_stats;
+    int64_t peak_in_flight;  /* most queries admitted at once */
+    int64_t peak_bytes;      /* most device-state bytes of admitted queries at once */
+} rpq_serve_stats_t;  /* (the struct tag, not a typedef, carries the name of the call below) */
 
 /* A server keeps the graph and every admitted query's state on the device;
  * queries arriving while others run are admitted as soon as a slot or lane
@@ -280,8 +344,16 @@ typedef struct rpq_serve_stats {
  * lanes, (2) advances every active lane by one level per step (a captured
  * CUDA graph replay), (3) retires lanes whose frontier emptied and stores
  * their answers.  Each answer is the same as the query alone would give.
- * Device memory is bounded by the slot/lane count (memory_budget is checked
- * at creation). */
+ * Memory-bounded admission: a queued query is admitted, in arrival order,
+ * only when its device state fits `memory_budget` beside that of the queries
+ * in flight -- engine 0: its workspace, the visited and three frontier
+ * bitsets of S' x ceil(n/64) words plus visited lists of S' x n ids (S' =
+ * its state count rounded up to a power of two, at least 4); engine 1: its
+ * bits in the four lane arrays, 4 x S x n bits (the lane arrays themselves
+ * are allocated whole at creation, sized by max_lanes and max_states).  A
+ * query that could never fit is refused at submission with RPQ_ERR_OOM.
+ * Engine 0 also sizes each query's share of the SMs by the load: a query
+ * admitted alone, with nothing queued, runs on the whole grid. */
 rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_config *cfg, rpq_server **out);
 
 /* Non-blocking.  RPQ_ERR_BUSY when the queue is full.  The automaton must
@@ -298,7 +370,10 @@ rpq_status rpq_serve_poll(rpq_server *s, uint64_t ticket, int32_t *out_vertices,
  * then RPQ_ERR_TIMEOUT). */
 rpq_status rpq_serve_drain(rpq_server *s, int64_t timeout_ms);
 
-rpq_status rpq_serve_stats_get(rpq_server *s, rpq_serve_stats *out);
+/* Server statistics (the counters above and the latency percentiles). */
+rpq_status rpq_serve_stats(rpq_server *s, struct rpq_serve_stats *out);
+/* The same call under its earlier name. */
+rpq_status rpq_serve_stats_get(rpq_server *s, struct rpq_serve_stats *out);
 void rpq_serve_destroy(rpq_server *s);
 
 /* ---------------------------------------------------------------- misc -- */

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 
+#include "graph.h"
 #include "rpq_internal.h"
 
 namespace rpq {
@@ -237,6 +238,149 @@ extern "C" rpq_status rpq_query(const rpq_graph *g, const rpq_nfa *nfa, int32_t 
     if (count > capacity)
         return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices, capacity %lld", (long long)count,
                     (long long)capacity);
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_query_multi(const rpq_graph *g, const rpq_nfa *nfa, int32_t n_sources,
+                                      const int32_t *sources, int32_t max_levels,
+                                      int32_t *out_vertices, int64_t capacity, int64_t *out_count,
+                                      rpq_stats *stats, void *stream) {
+    clear_error();
+    if (!g || !nfa || !out_count || n_sources < 0 || (n_sources > 0 && !sources))
+        return fail(RPQ_ERR_INVALID, "null argument");
+    if (capacity < 0 || (capacity > 0 && !out_vertices))
+        return fail(RPQ_ERR_INVALID, "bad output buffer");
+    if (max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
+    *out_count = 0;
+    if (stats) *stats = rpq_stats{};
+    if (n_sources == 0) return RPQ_OK;  // V_s empty: no pair at level 0, empty answer
+    if (is_device_pointer(sources)) return fail(RPQ_ERR_INVALID, "sources must be host memory");
+    rpq_graph *gm = const_cast<rpq_graph *>(g);
+    const bool dev = out_vertices && is_device_pointer(out_vertices);
+    QueryExtras x;
+    x.sources = sources;
+    x.n_sources = n_sources;
+    int64_t count = 0;
+    rpq_status s = run_query_ex(gm, nfa->a, &x, 0, max_levels, dev ? out_vertices : nullptr,
+                                capacity, nullptr, dev ? nullptr : out_vertices, stats, &count,
+                                stream, 1, !dev);
+    if (s != RPQ_OK) return s;
+    *out_count = count;
+    if (count > capacity)
+        return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices, capacity %lld", (long long)count,
+                    (long long)capacity);
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_query_sdr(const rpq_graph *g, const rpq_nfa *nfa, int32_t target,
+                                    int32_t max_levels, int32_t *out_vertices, int64_t capacity,
+                                    int64_t *out_count, rpq_stats *stats, void *stream) {
+    clear_error();
+    if (!g || !nfa || !out_count) return fail(RPQ_ERR_INVALID, "null argument");
+    if (capacity < 0 || (capacity > 0 && !out_vertices))
+        return fail(RPQ_ERR_INVALID, "bad output buffer");
+    *out_count = 0;
+    // section 4: SDR of N for v_f is SSR of the reversed automaton N^- from v_f
+    const Automaton rev = automaton_reverse(nfa->a);
+    rpq_graph *gm = const_cast<rpq_graph *>(g);
+    const bool dev = out_vertices && is_device_pointer(out_vertices);
+    int64_t count = 0;
+    rpq_status s = run_query(gm, rev, target, max_levels, dev ? out_vertices : nullptr, capacity,
+                             nullptr, dev ? nullptr : out_vertices, stats, &count, stream, !dev);
+    if (s != RPQ_OK) return s;
+    *out_count = count;
+    if (count > capacity)
+        return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices, capacity %lld", (long long)count,
+                    (long long)capacity);
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_query_levels(const rpq_graph *g, const rpq_nfa *nfa, int32_t n_sources,
+                                       const int32_t *sources, int32_t max_levels,
+                                       int32_t *out_vertices, int32_t *out_levels, int64_t capacity,
+                                       int64_t *out_count, void *stream) {
+    clear_error();
+    if (!g || !nfa || !out_count || n_sources < 0 || (n_sources > 0 && !sources))
+        return fail(RPQ_ERR_INVALID, "null argument");
+    if (capacity < 0 || (capacity > 0 && (!out_vertices || !out_levels)))
+        return fail(RPQ_ERR_INVALID, "bad output buffers");
+    if (max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
+    *out_count = 0;
+    if (n_sources == 0) return RPQ_OK;
+    if (is_device_pointer(sources)) return fail(RPQ_ERR_INVALID, "sources must be host memory");
+    const bool dv = out_vertices && is_device_pointer(out_vertices);
+    const bool dl = out_levels && is_device_pointer(out_levels);
+    if (capacity > 0 && dv != dl)
+        return fail(RPQ_ERR_INVALID, "out_vertices and out_levels must both be device or host memory");
+    rpq_graph *gm = const_cast<rpq_graph *>(g);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the answer and its levels are computed in device memory: the caller's
+    // or temporary buffers of n entries (an answer holds at most n vertices)
+    DevBuf tv, tl;
+    int32_t *v_dev = out_vertices, *l_dev = out_levels;
+    int64_t cap_dev = capacity;
+    if (!dv) {
+        if (!tv.alloc(sizeof(int32_t) * (size_t)g->n) || !tl.alloc(sizeof(int32_t) * (size_t)g->n))
+            return fail(RPQ_ERR_OOM, "answer buffers (%d entries)", g->n);
+        v_dev = tv.as<int32_t>();
+        l_dev = tl.as<int32_t>();
+        cap_dev = g->n;
+    }
+    QueryExtras x;
+    x.sources = sources;
+    x.n_sources = n_sources;
+    x.out_levels_dev = l_dev;
+    int64_t count = 0;
+    rpq_status s = run_query_ex(gm, nfa->a, &x, 0, max_levels, v_dev, cap_dev, nullptr, nullptr,
+                                nullptr, &count, stream, 1, false);
+    if (s != RPQ_OK) return s;
+    *out_count = count;
+    if (count > capacity)
+        return fail(RPQ_ERR_CAPACITY, "answer has %lld vertices, capacity %lld", (long long)count,
+                    (long long)capacity);
+    if (!dv && count > 0) {
+        RPQ_CUDA_TRY(cudaMemcpyAsync(out_vertices, v_dev, sizeof(int32_t) * (size_t)count,
+                                     cudaMemcpyDeviceToHost, st));
+        RPQ_CUDA_TRY(cudaMemcpyAsync(out_levels, l_dev, sizeof(int32_t) * (size_t)count,
+                                     cudaMemcpyDeviceToHost, st));
+        RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_query_witness(const rpq_graph *g, const rpq_nfa *nfa, int32_t n_sources,
+                                        const int32_t *sources, int32_t target, int32_t max_levels,
+                                        int32_t *path_vertices, int32_t *path_symbols,
+                                        int32_t capacity, int32_t *out_length, void *stream) {
+    clear_error();
+    if (!g || !nfa || !out_length || n_sources <= 0 || !sources)
+        return fail(RPQ_ERR_INVALID, "null argument or empty source set");
+    if (capacity < 0 || (capacity > 0 && (!path_vertices || !path_symbols)))
+        return fail(RPQ_ERR_INVALID, "bad output buffers");
+    if (target < 0 || target >= g->n)
+        return fail(RPQ_ERR_INVALID, "target %d outside [0, %d)", target, g->n);
+    if (max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
+    if (is_device_pointer(sources) || (capacity > 0 && (is_device_pointer(path_vertices) ||
+                                                        is_device_pointer(path_symbols))))
+        return fail(RPQ_ERR_INVALID, "sources and path buffers must be host memory");
+    *out_length = -1;
+    rpq_graph *gm = const_cast<rpq_graph *>(g);
+    QueryExtras x;
+    x.sources = sources;
+    x.n_sources = n_sources;
+    x.witness = true;
+    x.target = target;
+    x.path_v = path_vertices;
+    x.path_s = path_symbols;
+    x.path_cap = capacity;
+    int64_t count = 0;
+    rpq_status s = run_query_ex(gm, nfa->a, &x, 0, max_levels, nullptr, 0, nullptr, nullptr,
+                                nullptr, &count, stream, 1, false);
+    if (s != RPQ_OK) return s;
+    *out_length = x.path_len;
+    if (x.path_len >= 0 && x.path_len + 1 > capacity)
+        return fail(RPQ_ERR_CAPACITY, "witness has %d vertices, capacity %d", x.path_len + 1,
+                    capacity);
     return RPQ_OK;
 }
 

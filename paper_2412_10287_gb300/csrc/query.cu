@@ -109,6 +109,7 @@ struct Counters {
     unsigned long long claim_chunk[3], claim_item[3], claim_pull[3];
     unsigned long long srows_count[3];  // short rows listed per level slot
     long long answer_count;
+    long long vcount[kMaxStates];  // visited pairs per state when the query ended
 };
 
 // Where a level's counters live: device memory on grid levels or, while CTA
@@ -149,6 +150,10 @@ struct KParams {
     int32_t n, W, S;
     int32_t n_groups, n_units, n_targets, n_ugroups;
     int32_t source, max_levels;
+    // level 0 is Q_S x V_s: the vertices sources[0..n_sources) when sources
+    // is set (device memory; repeats allowed), else {source}
+    const int32_t *sources;
+    int32_t n_sources;
     uint64_t start_mask, final_mask;
     float alpha;       // pull when frontier edge mass * alpha > in-adjacency edges + rows
     int32_t min_pull;  // ... and the unit's source frontier holds at least this many pairs
@@ -173,6 +178,12 @@ struct KParams {
     long long row_cap, chunk_cap, srow_cap;
     unsigned long long *mf;  // [3][kMaxGroups]: frontier edge mass per group
     long long *fin_sums;     // [gridDim]
+    // a grid level that discovers at least sort_min pairs (0: never) has
+    // each state's new list range rewritten in ascending vertex order from
+    // its frontier bits, so that the rows of the next level are measured and
+    // expanded in address order; sort_cnt [S][gridDim] holds per-CTA counts
+    long long sort_min;
+    uint32_t *sort_cnt;
     Counters *c;
     // output
     int32_t *out_list;
@@ -183,6 +194,9 @@ struct KParams {
     unsigned long long *trace;
     int32_t trace_cap;
     QueryResult *result;  // host-mapped summary, or null
+    // when set ([S][n], -1 = not visited on entry): the level at which each
+    // visited pair was discovered, for path outputs (first reach, witness)
+    int32_t *pair_level;
     // tables inside the parameters: byte offsets into tab (when tab_inline)
     int32_t tab_inline, o_groups, o_units, o_tu, o_ts, o_ug;
     alignas(16) uint8_t tab[kInlineTables];
@@ -467,6 +481,7 @@ __device__ void load_tables(const KParams &p, const Shared &sh) {
 // ------------------------------------------------------------ discovery --
 struct LevelCtx {
     int slot;                     // slot of the level being discovered
+    int level;                    // the level being discovered
     const Ctrs *C;                // where its counters go
     int32_t *VL;
     const long long *vnext;       // first list entry of the level being discovered
@@ -532,6 +547,7 @@ __device__ __forceinline__ void warp_discover_batch(const KParams &p, const Leve
             }
             if (Fq)
                 atomicOr((unsigned long long *)(Fq + ((uint32_t)w[r] >> 6)), 1ull << (w[r] & 63));
+            if (p.pair_level) p.pair_level[(size_t)q2 * p.n + w[r]] = L.level;
         }
         run += __popc(m[r]);
     }
@@ -887,7 +903,7 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     const Ctrs &Cc = sh.cv[cur_smem ? 1 : 0];
     const Ctrs &Cn = sh.cv[on_grid ? 0 : 1];
     (void)s_acc;
-    LevelCtx L{ns, &Cn, p.VL, sh.vnext, on_grid ? p.F[ns] : nullptr};
+    LevelCtx L{ns, j + 1, &Cn, p.VL, sh.vnext, on_grid ? p.F[ns] : nullptr};
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
@@ -1211,6 +1227,108 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
             atomicMax(&p.trace[(size_t)j * kTraceFields + 11], t);
         }
     }
+}
+
+// Writes the set bits of words [w0, w1) of `bits` as ascending vertex ids to
+// out[0..), skipping positions at or past `limit` (CTA-wide; all threads).
+__device__ void compact_bits(const uint64_t *bits, int64_t w0, int64_t w1, int32_t *out,
+                             long long limit) {
+    __shared__ long long s_wsum[kWarps + 1];
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    long long run = 0;
+    for (int64_t base = w0; base < w1; base += kThreads) {
+        const int64_t wi = base + threadIdx.x;
+        uint64_t r = wi < w1 ? __ldcg(bits + wi) : 0ull;
+        const int32_t c = __popcll(r);
+        int32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long acc = 0;
+            for (int x = 0; x < kWarps; x++) {
+                const long long t = s_wsum[x];
+                s_wsum[x] = acc;
+                acc += t;
+            }
+            s_wsum[kWarps] = acc;
+        }
+        __syncthreads();
+        long long pos = run + s_wsum[warp] + incl - c;
+        while (r) {
+            const int b = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            if (pos < limit) out[pos] = (int32_t)(wi * 64 + b);
+            pos++;
+        }
+        run += s_wsum[kWarps];
+        __syncthreads();
+    }
+}
+
+// After grid level j (every CTA, after the barrier that closed it): when
+// the level discovered at least p.sort_min pairs, each state's new list
+// range VL[q][vnext[q], vnext[q] + n_q) is rewritten in ascending vertex
+// order from the frontier bits F_{j+1}[q] (which hold exactly those pairs):
+// per-CTA bit counts over contiguous word ranges, one barrier, then each CTA
+// writes its range's ids after the counts of the CTAs before it, and one
+// more barrier.  The range holds the same set, so nothing but the order
+// changes.  Returns false when a barrier failed.
+__device__ bool sort_level(const KParams &p, const Shared &sh, int j) {
+    const int ns = (j + 1) % 3;
+    __shared__ long long s_n[kMaxStates];
+    __shared__ long long s_tot;
+    if (threadIdx.x < p.S)
+        s_n[threadIdx.x] =
+            (long long)*(volatile unsigned long long *)&p.c->fl_count[ns][threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int q = 0; q < p.S; q++) t += s_n[q];
+        s_tot = t;
+    }
+    __syncthreads();
+    if (p.sort_min <= 0 || s_tot < p.sort_min) return true;  // uniform over the grid
+    const int64_t W = p.W;
+    const int64_t per = (W + gridDim.x - 1) / gridDim.x;
+    const int64_t w0 = min((int64_t)W, (int64_t)blockIdx.x * per);
+    const int64_t w1 = min((int64_t)W, w0 + per);
+    __shared__ unsigned long long s_c;
+    for (int q = 0; q < p.S; q++) {
+        if (!s_n[q]) continue;
+        const uint64_t *Fq = p.F[ns] + (size_t)q * W;
+        unsigned long long c = 0;
+        for (int64_t wi = w0 + threadIdx.x; wi < w1; wi += kThreads) c += __popcll(__ldcg(Fq + wi));
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+        if (threadIdx.x == 0) s_c = 0;
+        __syncthreads();
+        if (lane_id() == 0 && c) atomicAdd(&s_c, c);
+        __syncthreads();
+        if (threadIdx.x == 0) p.sort_cnt[(size_t)q * gridDim.x + blockIdx.x] = (uint32_t)s_c;
+    }
+    if (!grid_barrier(p.c)) return false;
+    __shared__ long long s_base;
+    for (int q = 0; q < p.S; q++) {
+        if (!s_n[q]) continue;
+        long long b = 0;
+        for (unsigned x = threadIdx.x; x < blockIdx.x; x += kThreads)
+            b += __ldcg(p.sort_cnt + (size_t)q * gridDim.x + x);
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(kFull, b, o);
+        if (threadIdx.x == 0) s_base = 0;
+        __syncthreads();
+        if (lane_id() == 0 && b) atomicAdd((unsigned long long *)&s_base, (unsigned long long)b);
+        __syncthreads();
+        const long long base = s_base;
+        __syncthreads();
+        compact_bits(p.F[ns] + (size_t)q * W, w0, w1, p.VL + (size_t)q * p.n + sh.vnext[q] + base,
+                     s_n[q] - base);
+    }
+    return grid_barrier(p.c);
 }
 
 // Level bookkeeping in shared memory, from the device counters of level j
@@ -1899,18 +2017,30 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             c->answer_count = 0;
             c->parked = 0;
         }
-        if (threadIdx.x < 32) {
-            // like every solo level, no frontier bits
-            LevelCtx L0{0, &sh.cv[1], p.VL, sh.vnext, nullptr};
-            const uint32_t swi = (uint32_t)p.source >> 6;
-            const uint64_t sbit = 1ull << (p.source & 63);
-            uint64_t sm = p.start_mask;
-            while (sm) {
-                const int q = __ffsll((long long)sm) - 1;
-                sm &= sm - 1;
-                if (lane_id() == 0)
-                    atomicOr((unsigned long long *)(p.P + (size_t)q * p.W + swi), sbit);
-                warp_discover(p, L0, lane_id() == 0, q, p.source);
+        {
+            // like every solo level, no frontier bits.  Each warp takes 32
+            // sources at a time; the lane whose atomicOr sets the bit of a
+            // start pair appends it (repeated sources are appended once)
+            LevelCtx L0{0, 0, &sh.cv[1], p.VL, sh.vnext, nullptr};
+            const int warp = threadIdx.x >> 5;
+            for (int base = warp * 32; base < p.n_sources; base += kThreads) {
+                const int i = base + (int)lane_id();
+                const bool have = i < p.n_sources;
+                const int32_t v = !have ? 0 : p.sources ? __ldg(p.sources + i) : p.source;
+                const uint32_t swi = (uint32_t)v >> 6;
+                const uint64_t sbit = 1ull << (v & 63);
+                uint64_t sm = p.start_mask;
+                while (sm) {
+                    const int q = __ffsll((long long)sm) - 1;
+                    sm &= sm - 1;
+                    bool found = false;
+                    if (have) {
+                        const unsigned long long old =
+                            atomicOr((unsigned long long *)(p.P + (size_t)q * p.W + swi), sbit);
+                        found = !(old & sbit);
+                    }
+                    warp_discover(p, L0, found, q, v);
+                }
             }
         }
         __syncthreads();
@@ -2004,6 +2134,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
                 // other parity's bit is clear, the barrier just passed takes
                 // no flags
                 if (lead && threadIdx.x == 0) atomicAnd(&p.c->gen_status, ~kOverflowBits);
+                if (!sort_level(p, sh, j)) return;
                 measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
                               s_acc);
                 if (!grid_barrier(p.c)) return;
@@ -2045,9 +2176,133 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         final_write(p, &s_claim);
         clear_state(p, sh, false, f_live, j, (int)blockIdx.x, (int)gridDim.x);
     }
-    if (lead) write_result(p, sh, solo_end);
+    if (lead) {
+        for (int q = threadIdx.x; q < p.S; q += kThreads)
+            p.c->vcount[q] = sh.vstart[q] + (long long)sh.fl[q];
+        write_result(p, sh, solo_end);
+    }
     if (p.trace && lead && threadIdx.x == 0)
         p.trace[(size_t)(p.trace_cap) * kTraceFields + 3] = global_timer_ns();
+}
+
+// ------------------------------------------------- path outputs (kernels) --
+// Level of first reach of every answer vertex: the smallest discovery level
+// over the final states' pairs of v (section 4: level k holds the pairs first
+// reached by words of length k, so this is the length of the shortest
+// accepted word labelling a 2-path from a source to v).
+__global__ void first_level_kernel(const int32_t *pair_level, int32_t n, uint64_t final_mask,
+                                   const int32_t *answer, int64_t count, int32_t *out_levels) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = answer[i];
+        int32_t best = INT32_MAX;
+        uint64_t fm = final_mask;
+        while (fm) {
+            const int q = __ffsll((long long)fm) - 1;
+            fm &= fm - 1;
+            const int32_t x = __ldg(pair_level + (size_t)q * n + v);
+            if (x >= 0 && x < best) best = x;
+        }
+        out_levels[i] = best;
+    }
+}
+
+// The pair levels of the query's visited pairs back to -1, through the
+// visited lists (their lengths per state are in the counters).
+__global__ void reset_levels_kernel(int32_t *pair_level, const int32_t *VL, int32_t n, int32_t S,
+                                    const Counters *c) {
+    for (int q = 0; q < S; q++) {
+        const long long cnt = c->vcount[q];
+        const int32_t *lst = VL + (size_t)q * n;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+             i += (long long)gridDim.x * blockDim.x)
+            pair_level[(size_t)q * n + __ldg(lst + i)] = -1;
+    }
+}
+
+// One transition q -d-> q' of the automaton, d a label direction of the graph.
+struct WTrans {
+    int32_t from, d, to;
+};
+
+// A shortest witness of `target` (one CTA): the final pair of the target with
+// the smallest level k, then, for k, k-1, ..., 1, a predecessor pair one
+// level lower: (q, u) with q -d-> q' and u a neighbour of v in the direction
+// inverse to d (the rows of G^d's transpose), i.e. the forward step walks
+// u -d-> v.  Among the candidates of a step the smallest (transition, row
+// position) is taken, so the result is deterministic.  Writes k + 1
+// vertices and k symbols (d, in [0, 2L)) when they fit in `cap` entries,
+// and the length k (-1: the target is not in the answer) to out[0].
+__global__ void witness_kernel(const DevAdj *adj, int32_t L, const int32_t *pair_level,
+                               int32_t n, uint64_t final_mask, const WTrans *tr, int32_t T,
+                               int32_t target, int32_t *path_v, int32_t *path_s, int32_t cap,
+                               int32_t *out) {
+    __shared__ int s_q, s_v, s_k;
+    __shared__ unsigned long long s_best;
+    if (threadIdx.x == 0) {
+        int best = INT32_MAX, bq = -1;
+        uint64_t fm = final_mask;
+        while (fm) {
+            const int q = __ffsll((long long)fm) - 1;
+            fm &= fm - 1;
+            const int32_t x = pair_level[(size_t)q * n + target];
+            if (x >= 0 && x < best) {
+                best = x;
+                bq = q;
+            }
+        }
+        s_k = bq < 0 ? -1 : best;
+        s_q = bq;
+        s_v = target;
+        out[0] = s_k;
+        if (s_k >= 0 && s_k < cap) path_v[s_k] = target;
+    }
+    __syncthreads();
+    const int k = s_k;
+    if (k < 0) return;
+    for (int step = k; step >= 1; step--) {
+        const int q2 = s_q;
+        const int32_t v = s_v;
+        if (threadIdx.x == 0) s_best = ~0ull;
+        __syncthreads();
+        for (int t = 0; t < T; t++) {
+            if (tr[t].to != q2) continue;  // uniform
+            const int q = tr[t].from, d = tr[t].d;
+            const DevAdj A = adj[d < L ? d + L : d - L];
+            int32_t b, e;
+            adj_row(A, v, b, e);
+            for (int32_t i = b + (int32_t)threadIdx.x; i < e; i += blockDim.x) {
+                const int32_t u = __ldg(A.nbr + i);
+                if (__ldg(pair_level + (size_t)q * n + u) == step - 1) {
+                    atomicMin(&s_best, ((unsigned long long)t << 32) | (uint32_t)i);
+                    break;
+                }
+            }
+            __syncthreads();
+            const bool found = s_best != ~0ull;
+            __syncthreads();  // every thread has read s_best before later atomics
+            if (found) break;
+        }
+        if (threadIdx.x == 0) {
+            const unsigned long long b = s_best;
+            if (b == ~0ull) {  // no predecessor: cannot happen for a visited pair
+                out[0] = -2;
+                s_v = -1;
+            } else {
+                const int t = (int)(b >> 32);
+                const int32_t u = __ldg(adj[tr[t].d < L ? tr[t].d + L : tr[t].d - L].nbr +
+                                        (int32_t)(b & 0xffffffffu));
+                if (k < cap) {
+                    path_v[step - 1] = u;
+                    path_s[step - 1] = tr[t].d;
+                }
+                s_q = tr[t].from;
+                s_v = u;
+            }
+        }
+        __syncthreads();
+        if (s_v < 0) return;
+    }
 }
 
 // ------------------------------------------------------------ host side --
@@ -2057,6 +2312,11 @@ struct QueryWorkspace : WorkspaceBase {
     long long row_cap = 0, chunk_cap = 0, srow_cap = 0;
     int32_t n = 0, W = 0;
     DevBuf P, F[3], VL, rows[3], cmap[3], srl[3], mf, fin, ctr, tables, out_list, trace;
+    DevBuf sortc;         // [S_cap][max grid] per-CTA counts of the sorted list rebuild
+    DevBuf srcs;          // the source set of the query (n_sources int32), grown on demand
+    DevBuf plevel;        // [S_cap][n] int32 pair levels, -1 between queries (path outputs)
+    DevBuf wtab, wout;    // witness: automaton transitions; path vertices, symbols, length
+    bool plevel_dirty = false;  // a failed query may have left pair levels set
     void *staging = nullptr;  // pinned host: tables upload + counters download
     size_t staging_bytes = 0;
     QueryResult *result_dev = nullptr;  // device address of the summary slot of staging
@@ -2117,6 +2377,7 @@ struct GridKey {
 std::map<GridKey, int> g_grid;
 std::mutex g_grid_mu;
 constexpr size_t kMaxDynSmem = 160 * 1024;
+constexpr int kMaxGrid = 152 * 64;  // CTAs of the persistent grid at most (per-CTA scratch)
 
 rpq_status get_launch_shape(int device, size_t smem, int *grid) {
     std::lock_guard<std::mutex> lk(g_grid_mu);
@@ -2157,7 +2418,8 @@ rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long
     ws->n = g->n;
     ws->W = (int32_t)W;
     bool ok = ws->P.alloc(bits) && ws->mf.alloc(sizeof(unsigned long long) * 3 * kMaxGroups) &&
-              ws->fin.alloc(sizeof(long long) * 152 * 64) && ws->ctr.alloc(sizeof(Counters)) &&
+              ws->fin.alloc(sizeof(long long) * kMaxGrid) && ws->ctr.alloc(sizeof(Counters)) &&
+              ws->sortc.alloc(sizeof(uint32_t) * (size_t)S_cap * kMaxGrid) &&
               ws->tables.alloc(kTablesBytes) && ws->VL.alloc(fl) &&
               ws->out_list.alloc(sizeof(int32_t) * (size_t)g->n);
     for (int k = 0; k < 3 && ok; k++)
@@ -2379,6 +2641,85 @@ float env_float(const char *name, float dflt) {
     return v ? (float)atof(v) : dflt;
 }
 
+// Big levels on big graphs: when the row offsets of a label no longer fit
+// the L2 cache (n >= 2^22 vertices: 16 MiB per label), a level's rows are
+// measured and expanded in vertex order after a level of at least
+// kSortPairs discoveries (sort_level); the discovery buffers then hand such
+// levels to the list pass early (kSortBuffer pairs per CTA).  Smaller graphs
+// keep discovery order.  RPQ_SORT_MIN (pairs, 0 = never) and
+// RPQ_DISCOVERY_BUFFER override.
+constexpr long long kSortPairs = 131072;
+constexpr int kSortBuffer = 1024;
+constexpr int32_t kSortVertices = 1 << 22;
+
+void sort_policy(const rpq_graph *g, KParams &p) {
+    const bool big = g->n >= kSortVertices;
+    p.sort_min = (long long)env_float("RPQ_SORT_MIN", big ? (float)kSortPairs : 0.0f);
+    const int dflt = p.sort_min > 0 ? kSortBuffer : kDisc;
+    // a smaller limit (tests) sends more levels down the grid-wide measure pass
+    p.disc_cap = std::min(kDisc, std::max(0, (int)env_float("RPQ_DISCOVERY_BUFFER", (float)dflt)));
+}
+
+// After a successful query with pair levels: the first-reach levels of the
+// answer (device list of `n_ans` entries), the witness path, then the pair
+// levels back to -1.  Stream-ordered after the traversal kernel.
+rpq_status path_outputs(const rpq_graph *g, const Automaton &a, QueryWorkspace *ws, QueryExtras *x,
+                        const int32_t *answer_dev, int64_t n_ans, cudaStream_t st) {
+    int dev_sms = 0;
+    RPQ_CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
+    if (x->out_levels_dev && n_ans > 0) {
+        const int blocks = (int)std::min<int64_t>((int64_t)dev_sms * 8, (n_ans + 255) / 256);
+        first_level_kernel<<<blocks, 256, 0, st>>>(ws->plevel.as<int32_t>(), g->n, a.final_mask,
+                                                    answer_dev, n_ans, x->out_levels_dev);
+        RPQ_CUDA_TRY(cudaGetLastError());
+        note_launch();
+    }
+    if (x->witness) {
+        std::vector<WTrans> tr;
+        for (size_t t = 0; t < a.from.size(); t++) {
+            const int s = a.sym[t];
+            const int lab = s < a.L ? s : s - a.L;
+            tr.push_back(WTrans{a.from[t], s < a.L ? lab : g->L + lab, a.to[t]});
+        }
+        const size_t tb = sizeof(WTrans) * std::max<size_t>(tr.size(), 1);
+        const int32_t cap = std::max(0, x->path_cap);
+        const size_t ob = sizeof(int32_t) * (2 * (size_t)cap + 1);
+        if ((ws->wtab.bytes < tb && !ws->wtab.alloc(tb)) || (ws->wout.bytes < ob && !ws->wout.alloc(ob)))
+            return fail(RPQ_ERR_OOM, "witness buffers");
+        if (!tr.empty())
+            RPQ_CUDA_TRY(cudaMemcpyAsync(ws->wtab.p, tr.data(), sizeof(WTrans) * tr.size(),
+                                         cudaMemcpyHostToDevice, st));
+        int32_t *wo = ws->wout.as<int32_t>();
+        witness_kernel<<<1, 256, 0, st>>>(g->d_adj.as<DevAdj>(), g->L, ws->plevel.as<int32_t>(),
+                                          g->n, a.final_mask, ws->wtab.as<WTrans>(),
+                                          (int32_t)tr.size(), x->target, wo + 1, wo + 1 + cap, cap,
+                                          wo);
+        RPQ_CUDA_TRY(cudaGetLastError());
+        note_launch();
+        int32_t len = -1;
+        RPQ_CUDA_TRY(cudaMemcpyAsync(&len, wo, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+        if (len < -1) return fail(RPQ_ERR_CUDA, "witness: a visited pair has no predecessor");
+        x->path_len = len;
+        if (len >= 0 && len < cap) {
+            RPQ_CUDA_TRY(cudaMemcpyAsync(x->path_v, wo + 1, sizeof(int32_t) * (size_t)(len + 1),
+                                         cudaMemcpyDeviceToHost, st));
+            if (len > 0)
+                RPQ_CUDA_TRY(cudaMemcpyAsync(x->path_s, wo + 1 + cap, sizeof(int32_t) * (size_t)len,
+                                             cudaMemcpyDeviceToHost, st));
+        }
+    }
+    {
+        const int blocks = dev_sms * 4;
+        reset_levels_kernel<<<blocks, 256, 0, st>>>(ws->plevel.as<int32_t>(), ws->VL.as<int32_t>(),
+                                                     g->n, a.S, ws->ctr.as<Counters>());
+        RPQ_CUDA_TRY(cudaGetLastError());
+        note_launch();
+    }
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
+    return RPQ_OK;
+}
+
 }  // namespace
 
 // Runs one query.  The answer goes to out_list_dev (device, `capacity`
@@ -2406,11 +2747,32 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
                           int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
                           int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
                           int grid_div, bool host_list) {
+    return run_query_ex(g, a, nullptr, source, max_levels, out_list_dev, capacity, out_bits_dev,
+                        out_host_list, stats, count, stream, grid_div, host_list);
+}
+
+// The query with its optional parts (x may be null): a source set instead of
+// the single source, first-reach levels of the answer, a witness path.
+rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_t source,
+                        int32_t max_levels, int32_t *out_list_dev, int64_t capacity,
+                        uint64_t *out_bits_dev, int32_t *out_host_list, rpq_stats *stats,
+                        int64_t *count, void *stream, int grid_div, bool host_list) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool want_host = !out_list_dev && (host_list || out_host_list);
     tl_answer.valid = false;  // a host answer lives until this thread's next query
-    if (source < 0 || source >= g->n)
+    const bool multi = x && x->sources;
+    const bool levels = x && (x->out_levels_dev || x->witness);
+    if (multi) {
+        if (x->n_sources <= 0) return fail(RPQ_ERR_INVALID, "empty source set");
+        for (int32_t i = 0; i < x->n_sources; i++)
+            if (x->sources[i] < 0 || x->sources[i] >= g->n)
+                return fail(RPQ_ERR_INVALID, "source %d (entry %d) outside [0, %d)", x->sources[i],
+                            i, g->n);
+    } else if (source < 0 || source >= g->n) {
         return fail(RPQ_ERR_INVALID, "source %d outside [0, %d)", source, g->n);
+    }
+    if (x && x->out_levels_dev && !out_list_dev)
+        return fail(RPQ_ERR_INVALID, "first-reach levels need the answer in device memory");
     if (max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
     if (a.S <= 0 || a.S > kMaxStates) return fail(RPQ_ERR_INVALID, "automaton has %d states", a.S);
     Tables t;
@@ -2435,16 +2797,41 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     p.n_units = (int32_t)t.units.size();
     p.n_targets = (int32_t)t.t_unit.size();
     p.n_ugroups = (int32_t)t.u_group.size();
-    p.source = source;
+    p.source = multi ? 0 : source;
+    p.n_sources = 1;
     p.max_levels = max_levels;
     p.start_mask = a.start_mask;
     p.final_mask = a.final_mask;
+    size_t src_bytes = 0;
+    if (multi) {
+        src_bytes = sizeof(int32_t) * (size_t)x->n_sources;
+        if (ws->srcs.bytes < src_bytes && !ws->srcs.alloc(src_bytes)) {
+            ws_release(g, std::move(ws));
+            return fail(RPQ_ERR_OOM, "source set (%d entries)", x->n_sources);
+        }
+        RPQ_CUDA_TRY(cudaMemcpyAsync(ws->srcs.p, x->sources, src_bytes, cudaMemcpyHostToDevice, st));
+        p.sources = ws->srcs.as<int32_t>();
+        p.n_sources = x->n_sources;
+    }
+    if (levels) {
+        const size_t pl_bytes = sizeof(int32_t) * (size_t)ws->S_cap * g->n;
+        if (ws->plevel.bytes < pl_bytes) {
+            if (!ws->plevel.alloc(pl_bytes)) {
+                ws_release(g, std::move(ws));
+                return fail(RPQ_ERR_OOM, "pair levels (%zu bytes)", pl_bytes);
+            }
+            ws->plevel_dirty = true;
+        }
+        if (ws->plevel_dirty) RPQ_CUDA_TRY(cudaMemsetAsync(ws->plevel.p, 0xff, pl_bytes, st));
+        ws->plevel_dirty = false;
+        p.pair_level = ws->plevel.as<int32_t>();
+    }
     p.alpha = env_float("RPQ_PULL_ALPHA", g->pull_alpha);
     p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
     p.solo_mass = (int32_t)env_float("RPQ_SOLO_MASS", (float)g->solo_mass);
     p.solo_items = (int32_t)env_float("RPQ_SOLO_ITEMS", (float)g->solo_items);
-    // a smaller limit (tests) sends more levels down the grid-wide measure pass
-    p.disc_cap = std::min(kDisc, std::max(0, (int)env_float("RPQ_DISCOVERY_BUFFER", (float)kDisc)));
+    sort_policy(g, p);
+    p.sort_cnt = ws->sortc.as<uint32_t>();
     p.epoch = ++ws->epoch;
     p.clear_first = ws->dirty ? 1 : 0;
     QueryResult *hr = reinterpret_cast<QueryResult *>(hs + kResultOffset);
@@ -2500,7 +2887,7 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
         ws_release(g, std::move(ws));
         return s;
     }
-    if (grid > 152 * 64) grid = 152 * 64;
+    if (grid > kMaxGrid) grid = kMaxGrid;
     if (grid_div > 1) grid = std::max(1, grid / grid_div);
     const bool timed = stats != nullptr;
     if (timed) RPQ_CUDA_TRY(cudaEventRecord(ws->ev0, st));
@@ -2519,6 +2906,7 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
         cudaMemsetAsync(ws->ctr.p, 0, sizeof(Counters), st);
         RPQ_CUDA_TRY(cudaStreamSynchronize(st));
         ws->dirty = true;
+        if (levels) ws->plevel_dirty = true;
         const int32_t hs_status = status_of(hc->gen_status);
         const rpq_status e = hs_status != 0 ? (rpq_status)hs_status : RPQ_ERR_CUDA;
         ws_release(g, std::move(ws));
@@ -2528,8 +2916,16 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
     *count = hr->answer_count;
     const bool copy_list = out_host_list && !out_list_dev && *count <= capacity && *count > 0;
     const int64_t host_bytes = want_host ? 4 * *count : 0;
+    if (levels) {
+        rpq_status e = path_outputs(g, a, ws.get(), x, out_list_dev, std::min<int64_t>(*count, capacity), st);
+        if (e != RPQ_OK) {
+            ws->plevel_dirty = true;
+            ws_release(g, std::move(ws));
+            return e;
+        }
+    }
     if (stats) {
-        stats->h2d_bytes = (int64_t)tab_bytes;
+        stats->h2d_bytes = (int64_t)(tab_bytes + src_bytes);
         stats->d2h_bytes = (int64_t)sizeof(QueryResult) + host_bytes;
         stats->levels = hr->levels;
         stats->visited_pairs = hr->visited;
@@ -2737,7 +3133,8 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     };
     const size_t x_ctr = take(sizeof(Counters));
     const size_t x_mf = take(sizeof(unsigned long long) * 3 * kMaxGroups);
-    const size_t x_fin = take(sizeof(long long) * 152 * 64);
+    const size_t x_fin = take(sizeof(long long) * kMaxGrid);
+    const size_t x_sort = take(sizeof(uint32_t) * (size_t)a.S * kMaxGrid);
     const size_t x_tab = take(std::max<size_t>(toff, 16));
     const size_t bits = sizeof(uint64_t) * (size_t)a.S * W;
     const size_t fl = sizeof(int32_t) * (size_t)a.S * g->n;
@@ -2772,6 +3169,7 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     p.n_targets = (int32_t)t.t_unit.size();
     p.n_ugroups = (int32_t)t.u_group.size();
     p.source = source;
+    p.n_sources = 1;
     p.max_levels = max_levels;
     p.start_mask = a.start_mask;
     p.final_mask = a.final_mask;
@@ -2779,7 +3177,8 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     p.min_pull = (int32_t)env_float("RPQ_PULL_MIN", (float)g->pull_min);
     p.solo_mass = g->solo_mass;
     p.solo_items = g->solo_items;
-    p.disc_cap = kDisc;
+    sort_policy(g, p);
+    p.sort_cnt = reinterpret_cast<uint32_t *>(base + x_sort);
     // the scratch layout moves with the automaton's size: clear P / F first
     p.clear_first = 1;
     p.groups = reinterpret_cast<const QGroup *>(base + x_tab + o_groups);

@@ -84,6 +84,28 @@ rpq_status run_query_slot(rpq_graph *g, const Automaton &a, int32_t source, int3
                           int32_t *out_list_dev, int64_t capacity, uint64_t *out_bits_dev,
                           int32_t *out_host_list, rpq_stats *stats, int64_t *count, void *stream,
                           int grid_div, bool host_list = false);
+// Optional parts of a query beyond the single-source answer (query.cu).
+struct QueryExtras {
+    // the source set V_s (host memory, n_sources >= 1 entries; repeats
+    // allowed); null for the single source of the call
+    const int32_t *sources = nullptr;
+    int32_t n_sources = 0;
+    // level of first reach of each answer vertex (device memory, one per
+    // answer entry); the answer itself must then go to device memory
+    int32_t *out_levels_dev = nullptr;
+    // a shortest witness of `target`: path_len + 1 vertices and path_len
+    // symbols into host memory of path_cap entries each; path_len = -1 when
+    // the target is not in the answer
+    bool witness = false;
+    int32_t target = 0;
+    int32_t *path_v = nullptr, *path_s = nullptr;
+    int32_t path_cap = 0;
+    int32_t path_len = -1;
+};
+rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_t source,
+                        int32_t max_levels, int32_t *out_list_dev, int64_t capacity,
+                        uint64_t *out_bits_dev, int32_t *out_host_list, rpq_stats *stats,
+                        int64_t *count, void *stream, int grid_div, bool host_list = false);
 // The calling thread's last host answer (run_query with a host list).
 rpq_status last_host_answer(const int32_t **answer, int64_t *count);
 

@@ -55,6 +55,7 @@ struct Done {
 struct Lane {
     bool busy = false;
     bool finished = false;
+    int64_t bytes = 0;  // device state counted against the memory budget
     uint64_t ticket = 0;
     Automaton a;
     int32_t source = 0;
@@ -90,6 +91,10 @@ struct rpq_server {
     bool stop = false;
     std::thread worker;
     uint64_t next_ticket = 1;
+    // admission: device state of the admitted queries against the budget
+    int64_t budget = 0;          // 0 = no limit
+    int64_t inflight_bytes = 0, peak_bytes = 0;
+    int inflight_n = 0, peak_inflight = 0;
     // statistics
     int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, level_steps = 0;
     std::vector<double> latency_ms;
@@ -100,6 +105,40 @@ struct rpq_server {
 
 namespace rpq {
 namespace {
+
+// Device state of one admitted query, the unit of memory-bounded
+// admission.  Engine 0: the query's workspace -- the visited bitset P and
+// three frontier bitsets of S_cap x ceil(n/64) words, and the visited lists of
+// S_cap x n ids (S_cap: the state count rounded up to a power of two, at
+// least 4, as workspaces are sized).  Engine 1: the query's bits in the four
+// lane arrays (M0, M1, P, NX): S x n bits each.
+int64_t query_bytes(const rpq_server *s, const Automaton &a) {
+    const int64_t n = s->g->n, W = (n + 63) / 64;
+    if (s->engine == 0) {
+        int64_t S = 4;
+        while (S < a.S) S *= 2;
+        return 4 * S * W * 8 + S * n * 4;
+    }
+    return 4 * (int64_t)a.S * ((n + 7) / 8);
+}
+
+bool fits_budget(const rpq_server *s, int64_t bytes) {
+    return s->budget <= 0 || s->inflight_bytes + bytes <= s->budget;
+}
+
+// caller holds s->mu
+void admit_account(rpq_server *s, int64_t bytes) {
+    s->inflight_bytes += bytes;
+    s->inflight_n++;
+    s->peak_bytes = std::max(s->peak_bytes, s->inflight_bytes);
+    s->peak_inflight = std::max(s->peak_inflight, s->inflight_n);
+    s->admitted++;
+}
+
+void retire_account(rpq_server *s, int64_t bytes) {
+    s->inflight_bytes -= bytes;
+    s->inflight_n--;
+}
 
 void lane_masks(const rpq_server *s, uint64_t active[kLW]) {
     for (int w = 0; w < kLW; w++) active[w] = 0;
@@ -175,29 +214,37 @@ void worker_main(rpq_server *s) {
                     if (s->lane[i].busy) return true;
                 return false;
             };
+            // (a queued query that does not fit the budget waits for a lane
+            // to retire, and some lane is then busy)
             s->cv.wait(lk, [&] { return s->stop || !s->queue.empty() || busy(); });
             if (s->stop) return;
-            // admission: free lanes take queued queries
+            // admission: free lanes take queued queries, in order, while
+            // their state fits the memory budget
             for (int i = 0; i < s->lanes_max && !s->queue.empty(); i++) {
                 if (s->lane[i].busy) continue;
-                Pending q = std::move(s->queue.front());
-                s->queue.pop_front();
-                if (q.a.start_mask == 0) {  // empty language from the start: empty answer
+                if (s->queue.front().a.start_mask == 0) {  // empty language: empty answer
+                    Pending q = std::move(s->queue.front());
+                    s->queue.pop_front();
                     finish_ticket(s, q.ticket, RPQ_OK, {}, q.t_submit);
                     s->cv_done.notify_all();
                     i--;
                     continue;
                 }
+                const int64_t need = query_bytes(s, s->queue.front().a);
+                if (!fits_budget(s, need)) break;
+                Pending q = std::move(s->queue.front());
+                s->queue.pop_front();
                 Lane &L = s->lane[i];
                 L.busy = true;
                 L.finished = false;
+                L.bytes = need;
                 L.ticket = q.ticket;
                 L.a = std::move(q.a);
                 L.source = q.source;
                 L.level = 0;
                 L.t_submit = q.t_submit;
                 admitted.push_back(i);
-                s->admitted++;
+                admit_account(s, need);
             }
         }
         rpq_status err = RPQ_OK;
@@ -308,6 +355,7 @@ void worker_main(rpq_server *s) {
                     Lane &L = s->lane[done_ids[k]];
                     std::vector<int32_t> a(ans.begin() + offs[k], ans.begin() + offs[k + 1]);
                     finish_ticket(s, L.ticket, RPQ_OK, std::move(a), L.t_submit);
+                    retire_account(s, L.bytes);
                     L.busy = false;
                     L.finished = false;
                 }
@@ -322,6 +370,7 @@ void worker_main(rpq_server *s) {
             for (int i = 0; i < s->lanes_max; i++)
                 if (s->lane[i].busy) {
                     finish_ticket(s, s->lane[i].ticket, err, {}, s->lane[i].t_submit);
+                    retire_account(s, s->lane[i].bytes);
                     s->lane[i].busy = false;
                 }
             while (!s->queue.empty()) {
@@ -334,8 +383,13 @@ void worker_main(rpq_server *s) {
     }
 }
 
-// Engine 0: one admitted query at a time per worker, on its own stream and
-// 1/lanes_max of the persistent grid.
+// Engine 0: one admitted query at a time per worker, on its own stream.  A
+// query is admitted when a worker is free and its workspace fits the memory
+// budget beside those of the queries in flight (in arrival order: a query
+// that does not fit waits, and so do the ones behind it).  Its share of the
+// persistent grid follows the load: a query that runs alone, with nothing
+// queued, takes the whole grid; otherwise 1/slots of it, so that up to
+// `slots` queries overlap on the device.
 void slot_worker_main(rpq_server *s) {
     cudaSetDevice(s->g->device);
     cudaStream_t st = nullptr;
@@ -347,25 +401,37 @@ void slot_worker_main(rpq_server *s) {
     std::vector<int32_t> buf((size_t)s->g->n);
     for (;;) {
         Pending q;
+        int64_t need = 0;
+        int grid_div = s->lanes_max;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            s->cv.wait(lk, [&] {
+                return s->stop ||
+                       (!s->queue.empty() && fits_budget(s, query_bytes(s, s->queue.front().a)));
+            });
             if (s->stop) break;
             q = std::move(s->queue.front());
             s->queue.pop_front();
-            s->admitted++;
+            need = query_bytes(s, q.a);
+            admit_account(s, need);
+            if (s->inflight_n == 1 && s->queue.empty()) grid_div = 1;
         }
         int64_t cnt = 0;
+        rpq_stats qs{};
         const rpq_status r = run_query_slot(s->g, q.a, q.source, s->max_levels, nullptr,
-                                            (int64_t)buf.size(), nullptr, buf.data(), nullptr,
-                                            &cnt, st, s->lanes_max);
+                                            (int64_t)buf.size(), nullptr, buf.data(), &qs, &cnt,
+                                            st, grid_div);
         std::vector<int32_t> ans;
         if (r == RPQ_OK) ans.assign(buf.begin(), buf.begin() + cnt);
         {
             std::lock_guard<std::mutex> lk(s->mu);
             finish_ticket(s, q.ticket, r, std::move(ans), q.t_submit);
-            s->level_steps++;
+            retire_account(s, need);
+            // the levels this query expanded: its non-empty levels after
+            // level 0, plus level 0 (the last expansion finds nothing)
+            if (r == RPQ_OK) s->level_steps += qs.levels + 1;
         }
+        s->cv.notify_all();  // a query waiting for memory may fit now
         s->cv_done.notify_all();
     }
     cudaStreamSynchronize(st);
@@ -396,11 +462,7 @@ extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_confi
         s->K = kMaxStates;
         s->max_levels = c.max_levels;
         s->queue_cap = c.queue_capacity > 0 ? (size_t)c.queue_capacity : 65536;
-        // a slot holds one query workspace: 4 bitsets + 3 vertex lists per state
-        const double per_slot = 16.0 * ((g->n + 63) / 64) * 8 * 4 + 16.0 * g->n * 4 * 3;
-        if (c.memory_budget > 0 && per_slot * slots > (double)c.memory_budget)
-            return fail(RPQ_ERR_OOM, "%d slots need about %.0f bytes, budget %lld", slots,
-                        per_slot * slots, (long long)c.memory_budget);
+        s->budget = c.memory_budget;
         rpq_server *raw = s.get();
         for (int k = 0; k < slots; k++) s->slot_workers.emplace_back(slot_worker_main, raw);
         *out = s.release();
@@ -414,17 +476,13 @@ extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_confi
     std::unique_ptr<rpq_server> s(new rpq_server());
     s->g = const_cast<rpq_graph *>(g);
     s->lanes_max = lanes;
+    s->engine = 1;
     s->max_levels = c.max_levels;
     s->queue_cap = c.queue_capacity > 0 ? (size_t)c.queue_capacity : 65536;
     RPQ_CUDA_TRY(cudaSetDevice(g->device));
-    // memory: the lane arrays dominate (4 arrays of n x K x 256 bits)
-    int Kc = 4;
-    while (Kc < K) Kc *= 2;
-    const double bytes = 4.0 * g->n * Kc * kLW * 8 + 4.0 * kLanes * ((g->n + 31) / 32) +
-                         3.0 * 4 * g->n + kServeTablesBytes;
-    if (c.memory_budget > 0 && bytes > (double)c.memory_budget)
-        return fail(RPQ_ERR_OOM, "server state needs %.0f bytes, budget %lld", bytes,
-                    (long long)c.memory_budget);
+    // the lane arrays are allocated whole (max_states slots of max_lanes
+    // lanes); the budget bounds the lane bits the admitted queries occupy
+    s->budget = c.memory_budget;
     rpq_status st = lane_ws_acquire_fixed(s->g, K, &s->ws);
     if (st != RPQ_OK) return st;
     s->K = s->ws->K;
@@ -477,6 +535,9 @@ extern "C" rpq_status rpq_serve_submit(rpq_server *s, const rpq_nfa *nfa, int32_
         const int lab = a.sym[t] < a.L ? a.sym[t] : a.sym[t] - a.L;
         if (lab >= s->g->L) return fail(RPQ_ERR_INVALID, "label %d is not a label of the graph", lab);
     }
+    if (s->budget > 0 && query_bytes(s, a) > s->budget)
+        return fail(RPQ_ERR_OOM, "the query needs %lld bytes of device state, budget %lld",
+                    (long long)query_bytes(s, a), (long long)s->budget);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->fatal != RPQ_OK) return fail(s->fatal, "server stopped after a device error");
     if (s->queue.size() >= s->queue_cap) {
@@ -542,16 +603,18 @@ extern "C" rpq_status rpq_serve_drain(rpq_server *s, int64_t timeout_ms) {
     return RPQ_OK;
 }
 
-extern "C" rpq_status rpq_serve_stats_get(rpq_server *s, rpq_serve_stats *out) {
+extern "C" rpq_status rpq_serve_stats_get(rpq_server *s, struct rpq_serve_stats *out) {
     clear_error();
     if (!s || !out) return fail(RPQ_ERR_INVALID, "null argument");
     std::lock_guard<std::mutex> lk(s->mu);
-    rpq_serve_stats r{};
+    rpq_serve_stats_t r{};
     r.submitted = s->submitted;
     r.admitted = s->admitted;
     r.completed = s->completed;
     r.rejected = s->rejected;
     r.level_steps = s->level_steps;
+    r.peak_in_flight = s->peak_inflight;
+    r.peak_bytes = s->peak_bytes;
     if (!s->latency_ms.empty()) {
         std::vector<double> v = s->latency_ms;
         std::sort(v.begin(), v.end());
@@ -567,6 +630,10 @@ extern "C" rpq_status rpq_serve_stats_get(rpq_server *s, rpq_serve_stats *out) {
     }
     *out = r;
     return RPQ_OK;
+}
+
+extern "C" rpq_status rpq_serve_stats(rpq_server *s, struct rpq_serve_stats *out) {
+    return rpq_serve_stats_get(s, out);
 }
 
 extern "C" void rpq_serve_destroy(rpq_server *s) {

@@ -33,9 +33,11 @@ EXPORTED = (
     "rpq_nfa_compile", "rpq_nfa_from_transitions", "rpq_nfa_free", "rpq_nfa_info",
     "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_last_answer",
     "rpq_query_noalloc",
-    "rpq_query_bitset",
+    "rpq_query_bitset", "rpq_query_multi", "rpq_query_sdr", "rpq_query_levels",
+    "rpq_query_witness",
     "rpq_query_batch", "rpq_serve_create", "rpq_serve_submit", "rpq_serve_poll",
-    "rpq_serve_drain", "rpq_serve_stats_get", "rpq_serve_destroy", "rpq_last_error",
+    "rpq_serve_drain", "rpq_serve_stats", "rpq_serve_stats_get", "rpq_serve_destroy",
+    "rpq_last_error",
     "rpq_version", "rpq_kernel_launches",
 )
 
@@ -69,7 +71,8 @@ class RpqServeStats(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("level_steps", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("elapsed_s", ctypes.c_double), ("qps", ctypes.c_double)]
+                ("elapsed_s", ctypes.c_double), ("qps", ctypes.c_double),
+                ("peak_in_flight", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -106,11 +109,16 @@ def lib():
             "rpq_last_answer": [p, p],
             "rpq_query_noalloc": [p, p, i32, i32, p, i64, p, p],
             "rpq_query_bitset": [p, p, i32, i32, p, p, p, p],
+            "rpq_query_multi": [p, p, i32, p, i32, p, i64, p, p, p],
+            "rpq_query_sdr": [p, p, i32, i32, p, i64, p, p, p],
+            "rpq_query_levels": [p, p, i32, p, i32, p, p, i64, p, p],
+            "rpq_query_witness": [p, p, i32, p, i32, i32, p, p, i32, p, p],
             "rpq_query_batch": [p, i32, p, p, i32, p, p, i64, p, p],
             "rpq_serve_create": [p, p, pp],
             "rpq_serve_submit": [p, p, i32, p],
             "rpq_serve_poll": [p, u64, p, i64, p],
             "rpq_serve_drain": [p, i64],
+            "rpq_serve_stats": [p, p],
             "rpq_serve_stats_get": [p, p],
         }
         for name, args in sig.items():
@@ -368,6 +376,83 @@ def rpq_query(g: Graph, nfa: Nfa, source: int, max_levels: int = 0, out=None, st
     return (res, st.as_dict()) if with_stats else res
 
 
+def _answer_call(call, out, with_stats):
+    """Shared marshalling of the calls that return one answer like rpq_query:
+    ``call(out_ptr, capacity, count_ref, stats_ref)``."""
+    st = RpqStats() if with_stats else None
+    cnt = ctypes.c_int64()
+    sp = ctypes.byref(st) if st is not None else None
+    if out is None:
+        _check(call(None, 0, ctypes.byref(cnt), sp), allow=(RPQ_ERR_CAPACITY,))
+        if cnt.value == 0:
+            res = np.empty(0, np.int32)
+        else:
+            ptr, n = ctypes.POINTER(ctypes.c_int32)(), ctypes.c_int64()
+            _check(lib().rpq_last_answer(ctypes.byref(ptr), ctypes.byref(n)))
+            res = np.ctypeslib.as_array(ptr, shape=(n.value,)).copy()
+    else:
+        _check(call(_ptr(out), out.numel(), ctypes.byref(cnt), sp))
+        res = int(cnt.value)
+    return (res, st.as_dict()) if with_stats else res
+
+
+def rpq_query_multi(g: Graph, nfa: Nfa, sources, max_levels: int = 0, out=None, stream=None,
+                    with_stats: bool = False):
+    """Query from a set of sources V_s (level 0 = Q_S x V_s): the vertices
+    reached from some source; same outputs as :func:`rpq_query`."""
+    src, psrc = _host_i32(sources)
+    return _answer_call(lambda o, c, n, sp: lib().rpq_query_multi(
+        g.h, nfa.h, src.size, psrc, int(max_levels), o, c, n, sp, _stream_handle(stream)),
+        out, with_stats)
+
+
+def rpq_query_sdr(g: Graph, nfa: Nfa, target: int, max_levels: int = 0, out=None, stream=None,
+                  with_stats: bool = False):
+    """Single-destination query: the vertices from which some 2-path to
+    ``target`` spells an accepted word; same outputs as :func:`rpq_query`."""
+    return _answer_call(lambda o, c, n, sp: lib().rpq_query_sdr(
+        g.h, nfa.h, int(target), int(max_levels), o, c, n, sp, _stream_handle(stream)),
+        out, with_stats)
+
+
+def rpq_query_levels(g: Graph, nfa: Nfa, sources, max_levels: int = 0, stream=None):
+    """Answer of the query from ``sources`` with each vertex's level of first
+    reach (the length of a shortest accepted word that labels a 2-path to
+    it); returns (vertices, levels) as int32 numpy arrays."""
+    src, psrc = _host_i32(sources)
+    cnt = ctypes.c_int64()
+    cap = g.n
+    v = np.empty(max(cap, 1), np.int32)
+    lv = np.empty(max(cap, 1), np.int32)
+    _check(lib().rpq_query_levels(g.h, nfa.h, src.size, psrc, int(max_levels), _ptr(v), _ptr(lv),
+                                  cap, ctypes.byref(cnt), _stream_handle(stream)))
+    return v[: cnt.value].copy(), lv[: cnt.value].copy()
+
+
+def rpq_query_witness(g: Graph, nfa: Nfa, sources, target: int, max_levels: int = 0,
+                      stream=None):
+    """A shortest witness of ``target``: (vertices, symbols) with k + 1
+    vertices from a source to the target and the k symbols of the word (a <
+    L: label a forward; a >= L: label a - L walked backwards), or None when
+    the target is not in the answer."""
+    src, psrc = _host_i32(sources)
+    cap = 1024
+    while True:
+        pv = np.empty(cap, np.int32)
+        ps = np.empty(cap, np.int32)
+        ln = ctypes.c_int32()
+        s = _check(lib().rpq_query_witness(g.h, nfa.h, src.size, psrc, int(target),
+                                           int(max_levels), _ptr(pv), _ptr(ps), cap,
+                                           ctypes.byref(ln), _stream_handle(stream)),
+                   allow=(RPQ_ERR_CAPACITY,))
+        if s == RPQ_OK:
+            break
+        cap = ln.value + 1
+    if ln.value < 0:
+        return None
+    return pv[: ln.value + 1].copy(), ps[: ln.value].copy()
+
+
 def rpq_query_noalloc(g: Graph, nfa: Nfa, source: int, out, max_levels: int = 0,
                       stream=None) -> int:
     """Single-source query through the entry point that allocates no device
@@ -457,7 +542,7 @@ class Server:
 
     def stats(self):
         st = RpqServeStats()
-        _check(lib().rpq_serve_stats_get(self.h, ctypes.byref(st)))
+        _check(lib().rpq_serve_stats(self.h, ctypes.byref(st)))
         return st.as_dict()
 
     def close(self):

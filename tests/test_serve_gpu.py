@@ -137,3 +137,35 @@ def test_serve_queue_limit_and_errors(setup, engine, width):
             srv.poll(10 ** 9)  # unknown ticket
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("engine,width", ENGINES, ids=ENGINE_IDS)
+def test_serve_memory_bounded_admission(setup, engine, width):
+    """A small memory budget admits fewer queries at once (the device state
+    of the admitted queries stays within it) and gives the same answers; a
+    query that could never fit is refused at submission."""
+    g, gg, og = setup
+    srcs = W.below(76, 1, 96, g.n).tolist()
+    texts = ["0*", "1/0*", "(0|1)*/2", "^0/1*"]  # DFAs of 1-2 states
+    jobs = [(R.rpq_nfa_compile(texts[i % 4], 4), srcs[i]) for i in range(96)]
+    exp = [og.ssr(oracle_compile(texts[i % 4], 4), srcs[i])["answer"].tolist() for i in range(96)]
+    W64 = (g.n + 63) // 64
+    per_query = (4 * 4 * W64 * 8 + 4 * g.n * 4) if engine == 0 else 4 * 2 * ((g.n + 7) // 8)
+    free = R.Server(gg, max_lanes=width, max_states=16, engine=engine)
+    tight = R.Server(gg, max_lanes=width, max_states=16, engine=engine,
+                     memory_budget=2 * per_query)
+    try:
+        got_free = run_server(free, jobs)
+        got_tight = run_server(tight, jobs)
+        assert [a.tolist() for a in got_free] == exp
+        assert [a.tolist() for a in got_tight] == exp
+        st_f, st_t = free.stats(), tight.stats()
+        assert st_t["peak_in_flight"] <= 2 and st_t["peak_bytes"] <= 2 * per_query
+        assert st_f["peak_in_flight"] > 2  # without the budget more run at once
+        big = R.rpq_nfa_compile("/".join(["0"] * 12), 4)  # 13 states: more than the budget
+        with pytest.raises(R.RpqError) as e:
+            tight.submit(big, srcs[0])
+        assert e.value.status == R.RPQ_ERR_OOM
+    finally:
+        free.close()
+        tight.close()
