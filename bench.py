@@ -732,8 +732,9 @@ def run_extras(args, R, torch):
 def run_profile_sample(args):
     """The launches an ncu DRAM capture takes: every query of the workload
     once (skipped by the capture: `-s` = the number of queries), then the
-    `--profile-sample` queries with the most algorithmic bytes again, whose
-    algorithmic and push-model bytes go to `--sample-out`.  The push/pull
+    `--profile-sample` queries with the longest device time again (they
+    dominate the mean launch), whose algorithmic and push-model bytes go to
+    `--sample-out`.  The push/pull
     setting is the library's default or the RPQ_PULL_* / RPQ_SOLO_*
     environment variables (no autotuning launches before the capture)."""
     import torch
@@ -756,8 +757,9 @@ def run_profile_sample(args):
     for nfa, q in zip(nfas, w.queries):
         _, st = R.rpq_query(gg, nfa, q.source, out=out, stream=stream, with_stats=True)
         S = nfa.info()[0]
-        alg.append((st["push_bytes"] + 3 * S * W_words * 8 * (st["levels"] + 1), st["push_bytes"]))
-    pick = sorted(range(len(alg)), key=lambda i: -alg[i][0])[:args.profile_sample]
+        alg.append((st["push_bytes"] + 3 * S * W_words * 8 * (st["levels"] + 1), st["push_bytes"],
+                    st["device_ms"]))
+    pick = sorted(range(len(alg)), key=lambda i: -alg[i][2])[:args.profile_sample]
     for i in pick:
         R.rpq_query(gg, nfas[i], w.queries[i].source, out=out, stream=stream)
     torch.cuda.synchronize()
@@ -765,8 +767,9 @@ def run_profile_sample(args):
            "queries": [[w.queries[i].regex, w.queries[i].source] for i in pick],
            "algorithmic_bytes": [alg[i][0] for i in pick],
            "push_bytes": [alg[i][1] for i in pick],
-           "sample": f"the {len(pick)} of the {len(nfas)} {name} queries with the most "
-                     "algorithmic bytes, captured after one pass over all of them"}
+           "device_ms": [alg[i][2] for i in pick],
+           "sample": f"the {len(pick)} of the {len(nfas)} {name} queries with the longest "
+                     "device time, captured after one pass over all of them"}
     os.makedirs(os.path.dirname(os.path.abspath(args.sample_out)), exist_ok=True)
     with open(args.sample_out, "w") as f:
         json.dump(rec, f)

@@ -76,8 +76,12 @@ typedef struct rpq_stats {
 
 /* Replace the device allocator used for graphs and workspaces (for example
  * with PyTorch's caching allocator).  alloc(size, ctx) returns device memory
- * or NULL; free(ptr, ctx) releases it.  Pass NULLs to restore cudaMalloc /
- * cudaFree.  Must be called while no graph or server exists. */
+ * or NULL (the library then fails the call with RPQ_ERR_OOM and keeps
+ * working); free(ptr, ctx) releases it.  Pass NULLs to restore cudaMalloc /
+ * cudaFree.  The change applies to later allocations; every buffer goes
+ * back to the allocator that made it, so the allocator may be changed while
+ * graphs exist.  The callbacks may be called from the library's worker
+ * threads (batch and server slots). */
 rpq_status rpq_set_allocator(void *(*alloc)(size_t size, void *ctx),
                              void (*free_fn)(void *ptr, void *ctx), void *ctx);
 
@@ -125,6 +129,17 @@ rpq_status rpq_graph_export(const rpq_graph *g, int32_t label, int32_t inverse,
 rpq_status rpq_graph_autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
                               const int32_t *sources, float *alpha_out, int32_t *min_pull_out,
                               int32_t *solo_mass_out, void *stream);
+
+/* The hybrid of section 5.1: Algorithm 2 (section 4: no traversal matrix;
+ * every step expands the whole visited set P) while P holds fewer than
+ * `switch_pairs` (state, vertex) pairs, then Algorithm 1 from the pairs the
+ * last step found (the paper's constant is 100).  Algorithm 2 steps run on
+ * one CTA of the persistent kernel, push only.  Answers, levels and visited
+ * counts never change; the expanded-pair, product-edge and push-byte
+ * counters then count the re-expanded pairs too.  0 (the default) runs
+ * Algorithm 1 throughout.  Applies to later queries on g (RPQ_ALG2_SWITCH
+ * overrides). */
+rpq_status rpq_graph_set_hybrid(rpq_graph *g, int64_t switch_pairs);
 
 /* ---------------------------------------------------------- automaton -- */
 
@@ -333,6 +348,8 @@ typedef struct rpq_serve_stats {
     double qps;              /* completed / elapsed_s */
     int64_t peak_in_flight;  /* most queries admitted at once */
     int64_t peak_bytes;      /* most device-state bytes of admitted queries at once */
+    int64_t oom_retries;     /* engine 0: queries put back in the queue after a device
+                                allocation failed beside other queries in flight */
 } rpq_serve_stats_t;  /* (the struct tag, not a typedef, carries the name of the call below) */
 
 /* A server keeps the graph and every admitted query's state on the device;
@@ -353,7 +370,11 @@ typedef struct rpq_serve_stats {
  * are allocated whole at creation, sized by max_lanes and max_states).  A
  * query that could never fit is refused at submission with RPQ_ERR_OOM.
  * Engine 0 also sizes each query's share of the SMs by the load: a query
- * admitted alone, with nothing queued, runs on the whole grid. */
+ * admitted alone, with nothing queued, runs on the whole grid.  When a
+ * query's device allocation fails while other queries are in flight, engine
+ * 0 puts it back at the head of the queue and admits fewer queries at once
+ * (raised again as queries complete); a query that fails alone completes
+ * with RPQ_ERR_OOM. */
 rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_config *cfg, rpq_server **out);
 
 /* Non-blocking.  RPQ_ERR_BUSY when the queue is full.  The automaton must

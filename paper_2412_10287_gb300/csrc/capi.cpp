@@ -19,11 +19,7 @@ namespace rpq {
 namespace {
 thread_local std::string t_error;
 
-struct Allocator {
-    void *(*alloc)(size_t, void *) = nullptr;
-    void (*free_fn)(void *, void *) = nullptr;
-    void *ctx = nullptr;
-};
+std::mutex g_alloc_mu;
 Allocator g_alloc;
 std::atomic<int64_t> g_live_objects{0};
 }  // namespace
@@ -42,8 +38,14 @@ void clear_error() { t_error.clear(); }
 
 const char *rpq_last_error_str() { return t_error.c_str(); }
 
-void *dev_alloc(size_t bytes) {
-    if (g_alloc.alloc) return g_alloc.alloc(bytes, g_alloc.ctx);
+void *dev_alloc(size_t bytes, Allocator *used) {
+    Allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    *used = a;
+    if (a.alloc) return a.alloc(bytes, a.ctx);
     void *p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -52,9 +54,9 @@ void *dev_alloc(size_t bytes) {
     return p;
 }
 
-void dev_free(void *p) {
+void dev_free(void *p, const Allocator &used) {
     if (!p) return;
-    if (g_alloc.free_fn) g_alloc.free_fn(p, g_alloc.ctx);
+    if (used.free_fn) used.free_fn(p, used.ctx);
     else cudaFree(p);
 }
 
@@ -88,6 +90,7 @@ extern "C" rpq_status rpq_set_allocator(void *(*alloc)(size_t, void *), void (*f
     clear_error();
     if ((alloc == nullptr) != (free_fn == nullptr))
         return fail(RPQ_ERR_INVALID, "alloc and free must both be set or both be null");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
     g_alloc.alloc = alloc;
     g_alloc.free_fn = free_fn;
     g_alloc.ctx = ctx;

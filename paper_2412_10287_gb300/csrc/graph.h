@@ -46,6 +46,8 @@ struct rpq_graph {
     // and frontier items stay within these (solo_mass < 0: never)
     int32_t solo_mass = 2048;
     int32_t solo_items = 256;
+    // Algorithm 2 while the visited set is smaller than this (0: never)
+    int64_t alg2_until = 0;
 
     std::mutex ws_mu;
     std::vector<std::unique_ptr<rpq::WorkspaceBase>> ws_free;

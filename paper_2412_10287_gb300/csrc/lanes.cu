@@ -600,12 +600,16 @@ rpq_status lane_ws_alloc(LaneWorkspace *ws, const rpq_graph *g, int K) {
         !ws->cnt.alloc(sizeof(int64_t) * (kLanes * chunks + 1)) ||
         !ws->pos.alloc(sizeof(int64_t) * (kLanes * chunks + 1)))
         return fail(RPQ_ERR_OOM, "lane workspace (%d slots)", K);
-    RPQ_CUDA_TRY(cudaMemset(ws->NX.p, 0, words * 8));
-    RPQ_CUDA_TRY(cudaMemset(ws->M0.p, 0, words * 8));
-    RPQ_CUDA_TRY(cudaMemset(ws->M1.p, 0, words * 8));
-    RPQ_CUDA_TRY(cudaMemset(ws->P.p, 0, words * 8));
-    RPQ_CUDA_TRY(cudaMemset(ws->tv.p, 0, tvw * 8));
-    RPQ_CUDA_TRY(cudaMemset(ws->ctr.p, 0, sizeof(LaneCounters)));
+    // cleared before any stream uses the workspace: a plain cudaMemset is
+    // ordered only on the legacy default stream, which non-blocking streams
+    // (the server's) do not wait for
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->NX.p, 0, words * 8, 0));
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->M0.p, 0, words * 8, 0));
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->M1.p, 0, words * 8, 0));
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->P.p, 0, words * 8, 0));
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->tv.p, 0, tvw * 8, 0));
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->ctr.p, 0, sizeof(LaneCounters), 0));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(0));
     ws->staging_bytes = (1 << 20) + 4096;
     RPQ_CUDA_TRY(cudaMallocHost(&ws->staging, ws->staging_bytes));
     return RPQ_OK;

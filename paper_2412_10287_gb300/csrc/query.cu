@@ -63,7 +63,7 @@ constexpr int kGather = 1024;         // gather buffer entries per CTA
 constexpr int kMaxGroups = 512;
 constexpr int kMaxUnits = 512;
 constexpr int kMaxTargets = 2048;
-constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;
+constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // default limit of every device wait
 
 // (source state q, direction d) with the targets delta(q, d) as a mask.
 struct QGroup {
@@ -160,6 +160,10 @@ struct KParams {
     int32_t solo_mass;   // a level runs on CTA 0 alone when its push edge mass <= this,
     int32_t solo_items;  // its frontier items <= this and no unit pulls (solo_mass < 0: never)
     uint32_t epoch;      // distinct per launch on this workspace (tags the gate word)
+    uint64_t wait_ns;    // limit of every wait on other CTAs (then RPQ_ERR_TIMEOUT)
+    // failure test: the last CTA leaves at its first release from the gate,
+    // so the grid's next barrier waits for it until the limit runs out
+    int32_t test_leave;
     int32_t clear_first; // P and F hold garbage: clear them before the traversal
     int32_t disc_cap;    // a CTA measures its own discoveries when at most this many (<= kDisc)
     // automaton tables (device)
@@ -184,6 +188,10 @@ struct KParams {
     // expanded in address order; sort_cnt [S][gridDim] holds per-CTA counts
     long long sort_min;
     uint32_t *sort_cnt;
+    // Algorithm 2 (section 4, no traversal matrix) while the visited set
+    // holds fewer than alg2_until pairs, then Algorithm 1 (the hybrid switch
+    // of section 5.1); 0 = Algorithm 1 throughout
+    long long alg2_until;
     Counters *c;
     // output
     int32_t *out_list;
@@ -245,7 +253,8 @@ __device__ __forceinline__ void set_status(Counters *c, int32_t err) {
 
 // Grid barrier: -1 when the query failed, else 1 when some CTA (this one
 // with `overflow`) flagged a discovery-buffer overflow on arriving, else 0.
-__device__ __forceinline__ int grid_sync(Counters *c, bool overflow = false) {
+__device__ __forceinline__ int grid_sync(const KParams &p, bool overflow = false) {
+    Counters *c = p.c;
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -267,7 +276,7 @@ __device__ __forceinline__ int grid_sync(Counters *c, bool overflow = false) {
             for (unsigned it = 1;; it++) {
                 asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(w) : "l"(&c->gen_status) : "memory");
                 if ((unsigned)(w >> 32) != gen || status_of(w) != 0) break;
-                if ((it & 255u) == 0 && global_timer_ns() - t0 > kBarrierTimeoutNs) {
+                if ((it & 255u) == 0 && global_timer_ns() - t0 > p.wait_ns) {
                     set_status(c, (int32_t)RPQ_ERR_TIMEOUT);
                     w = 1;
                     break;
@@ -280,7 +289,7 @@ __device__ __forceinline__ int grid_sync(Counters *c, bool overflow = false) {
     return s_ok;
 }
 
-__device__ __forceinline__ bool grid_barrier(Counters *c) { return grid_sync(c) >= 0; }
+__device__ __forceinline__ bool grid_barrier(const KParams &p) { return grid_sync(p) >= 0; }
 
 // ------------------------------------------------------- shared layout ---
 // Per-query tables live in shared memory for the whole kernel, so that the
@@ -687,13 +696,20 @@ __device__ __forceinline__ void measure_flush(const KParams &p, const Shared &sh
 // side by side, each lane with its kR lookups in flight together; then this
 // CTA's sums of edge mass and push bytes / product edges go to the slot's
 // counters.
+// With `all`, every visited pair is measured instead (the whole list of each
+// state, VL[q][0, vnext[q] + n_q)): the frontier of an Algorithm 2 step.
 __device__ void measure_level(const KParams &p, const Shared &sh, const Ctrs &C, int slot, int cta,
-                              int ncta, unsigned long long *s_acc) {
+                              int ncta, unsigned long long *s_acc, bool all = false) {
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    __shared__ long long s_cnt[kMaxStates];  // new pairs per state, read in one round trip
-    if (threadIdx.x < p.S)
-        s_cnt[threadIdx.x] = (long long)*(volatile unsigned long long *)&C.fl[slot * kMaxStates + threadIdx.x];
+    __shared__ long long s_cnt[kMaxStates];  // pairs per state, read in one round trip
+    __shared__ long long s_first[kMaxStates];  // their first list entry
+    if (threadIdx.x < p.S) {
+        const long long fresh =
+            (long long)*(volatile unsigned long long *)&C.fl[slot * kMaxStates + threadIdx.x];
+        s_cnt[threadIdx.x] = all ? sh.vnext[threadIdx.x] + fresh : fresh;
+        s_first[threadIdx.x] = all ? 0 : sh.vnext[threadIdx.x];
+    }
     __syncthreads();
     // bpre[g] = batches of the groups before g (kept in the gather buffer,
     // idle between expansions); batch b goes to warp b / ncta of CTA b % ncta
@@ -726,7 +742,7 @@ __device__ void measure_level(const KParams &p, const Shared &sh, const Ctrs &C,
         const int g = lo, q = sh.gq[g];
         const long long cnt = s_cnt[q];
         const long long b0 = (long long)(b - bpre[g]) * 32 * kR;
-        const int32_t *lst = p.VL + (size_t)q * p.n + sh.vnext[q];
+        const int32_t *lst = p.VL + (size_t)q * p.n + s_first[q];
         bool ok[kR];
         int32_t w[kR];
 #pragma unroll
@@ -993,94 +1009,78 @@ __device__ void expand_phase(const KParams &p, int j, const Shared &sh, const in
     trace_put(p, j, 8, global_timer_ns());
     // (2) short rows of push groups: first the level's short-row list
     //     (hypersparse groups: only non-empty rows, ranges known), then the
-    //     frontier items of dense groups (row found by its offsets); CTA
-    //     tiles of them, scan-based gather; a small level is spread over
-    //     every CTA (tiles of 8 to kThreads items)
-    const long long n_listed = sh.nsrow[0];
-    const long long total_items = n_listed + sh.dpref[p.n_groups];
-    const int4 *SRL = p.srl[cs];
-    const long long item_tile =
-        min((long long)kThreads, max(8LL, ((total_items + ncta - 1) / ncta + 7) & ~7LL));
-    TileClaims item_claims(&p.c->claim_item[cs], item_tile, cta, ncta);
-    while (total_items > 0) {
-        const long long t0 = item_claims.take(s_claim, total_items);
-        if (t0 >= total_items) break;
-        const long long i = t0 + threadIdx.x;
-        int g = -1;
-        int32_t rb = 0, re = 0;
-        if (threadIdx.x < item_tile && i < n_listed) {
-            const int4 e = __ldcg(SRL + i);
-            g = e.x;
-            if (sh.tpush[g]) {  // rows of groups that pull this level are skipped
-                rb = e.y;
-                re = e.z;
+    //     frontier items of dense groups (row found by its offsets).  Each
+    //     warp takes batches of 32 items (batch b to warp b / ncta of CTA
+    //     b % ncta, so a small level spreads over every CTA), scans their
+    //     degrees (< kWarpRow each) with shuffles and walks the batch's edges
+    //     32 x kR at a time; the row of an edge is found by a binary search
+    //     over the lanes' inclusive sums.  No CTA barrier: every warp keeps
+    //     its own loads in flight.
+    {
+        const long long n_listed = sh.nsrow[0];
+        const long long total_items = n_listed + sh.dpref[p.n_groups];
+        const int4 *SRL = p.srl[cs];
+        const long long nbatch = (total_items + 31) / 32;
+        const long long stride = (long long)ncta * kWarps;
+        for (long long bt = (long long)cta + (long long)warp * ncta; bt < nbatch; bt += stride) {
+            const long long i = bt * 32 + lane;
+            int g = 0;
+            int32_t rb = 0, re = 0;
+            if (i < n_listed) {
+                const int4 e = __ldcg(SRL + i);
+                g = e.x;
+                if (sh.tpush[g]) {  // rows of groups that pull this level are skipped
+                    rb = e.y;
+                    re = e.z;
+                }
+            } else if (i < total_items) {
+                const long long k = i - n_listed;
+                int lo = 0, hi = p.n_groups - 1;  // last group with dpref <= k
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sh.dpref[mid] <= k) lo = mid; else hi = mid - 1;
+                }
+                g = lo;
+                const int q = sh.gq[g];
+                const int32_t v = __ldcg(p.VL + (size_t)q * p.n + sh.vstart[q] + (k - sh.dpref[g]));
+                const int32_t *off = p.adj[sh.gd[g]].off;
+                rb = __ldg(off + v);
+                re = __ldg(off + v + 1);
+                if (re - rb >= kWarpRow) re = rb;  // expanded through the chunk list
             }
-        } else if (threadIdx.x < item_tile && i < total_items) {
-            const long long k = i - n_listed;
-            int lo = 0, hi = p.n_groups - 1;  // last group with dpref <= k
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sh.dpref[mid] <= k) lo = mid; else hi = mid - 1;
-            }
-            g = lo;
-            const int q = sh.gq[g];
-            const int32_t v = __ldcg(p.VL + (size_t)q * p.n + sh.vstart[q] + (k - sh.dpref[g]));
-            const int32_t *off = p.adj[sh.gd[g]].off;
-            rb = __ldg(off + v);
-            re = __ldg(off + v + 1);
-            if (re - rb >= kWarpRow) re = rb;  // expanded through the chunk list
-        }
-        const int32_t deg = re - rb;
-        __shared__ int32_t wsum[kWarps + 1];
-        int32_t incl = deg;
+            const int32_t deg = re - rb;
+            int32_t incl = deg;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(kFull, incl, o);
-            if ((int)lane >= o) incl += y;
-        }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int32_t run = 0;
-            for (int x = 0; x < kWarps; x++) {
-                const int32_t s = wsum[x];
-                wsum[x] = run;
-                run += s;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, incl, o);
+                if ((int)lane >= o) incl += y;
             }
-            wsum[kWarps] = run;
-        }
-        __syncthreads();
-        const int32_t excl = wsum[warp] + incl - deg;
-        const long long tot = wsum[kWarps];
-        __syncthreads();
-        for (long long rbase = 0; rbase < tot; rbase += kGather) {
-            const long long lo = max((long long)excl, rbase);
-            const long long hi = min((long long)excl + deg, rbase + kGather);
-            for (long long r = lo; r < hi; r++) {
-                sh.gbuf_k[r - rbase] = rb + (int32_t)(r - excl);
-                sh.gbuf_g[r - rbase] = (int16_t)g;
-            }
-            __syncthreads();
-            const long long cnt = min((long long)kGather, tot - rbase);
-            for (long long base = 0; base < cnt; base += (long long)kThreads * kR) {
+            const int32_t excl = incl - deg;
+            const int32_t tot = __shfl_sync(kFull, incl, 31);
+            for (int32_t base = 0; base < tot; base += 32 * kR) {
                 bool valid[kR];
                 uint64_t tm[kR];
                 int32_t w[kR];
 #pragma unroll
                 for (int r = 0; r < kR; r++) {
-                    const long long idx = base + (long long)r * kThreads + threadIdx.x;
-                    valid[r] = idx < cnt;
-                    w[r] = 0;
-                    tm[r] = 0;
-                    if (valid[r]) {
-                        const int gg = sh.gbuf_g[idx];
-                        w[r] = __ldg(sh.gnbr[gg] + sh.gbuf_k[idx]);
-                        tm[r] = sh.tpush[gg];
+                    const int32_t e = base + r * 32 + (int32_t)lane;
+                    // owner: the first lane whose inclusive sum exceeds e
+                    int own = 0;
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1) {
+                        const int32_t x = __shfl_sync(kFull, incl, own + st - 1);
+                        if (x <= e) own += st;
                     }
+                    own = min(own, 31);
+                    const int32_t orb = __shfl_sync(kFull, rb, own);
+                    const int32_t oex = __shfl_sync(kFull, excl, own);
+                    const int og = __shfl_sync(kFull, g, own);
+                    valid[r] = e < tot;
+                    w[r] = valid[r] ? __ldg(sh.gnbr[og] + orb + (e - oex)) : 0;
+                    tm[r] = valid[r] ? sh.tpush[og] : 0ull;
                 }
                 relax_batch(p, sh, gsf, L, valid, tm, w);
             }
-            __syncthreads();
         }
     }
 
@@ -1311,7 +1311,7 @@ __device__ bool sort_level(const KParams &p, const Shared &sh, int j) {
         __syncthreads();
         if (threadIdx.x == 0) p.sort_cnt[(size_t)q * gridDim.x + blockIdx.x] = (uint32_t)s_c;
     }
-    if (!grid_barrier(p.c)) return false;
+    if (!grid_barrier(p)) return false;
     __shared__ long long s_base;
     for (int q = 0; q < p.S; q++) {
         if (!s_n[q]) continue;
@@ -1328,7 +1328,7 @@ __device__ bool sort_level(const KParams &p, const Shared &sh, int j) {
         compact_bits(p.F[ns] + (size_t)q * W, w0, w1, p.VL + (size_t)q * p.n + sh.vnext[q] + base,
                      s_n[q] - base);
     }
-    return grid_barrier(p.c);
+    return grid_barrier(p);
 }
 
 // Level bookkeeping in shared memory, from the device counters of level j
@@ -1353,13 +1353,25 @@ __device__ __forceinline__ void level_advance(const KParams &p, int j, const Sha
         lb = *(volatile unsigned long long *)&C.bytes[cs];
         le = *(volatile unsigned long long *)&C.edges[cs];
     }
+    const bool a2 = sh.flags[1] != 0;
     __syncthreads();
     if (t < kMaxStates) {
-        sh.fl_prev[t] = sh.fl[t];
-        sh.vprev[t] = sh.vstart[t];
-        sh.vstart[t] += (long long)sh.fl[t];
-        sh.fl[t] = fv;
-        sh.vnext[t] = sh.vstart[t] + (long long)fv;
+        if (a2) {
+            // an Algorithm 2 step expands every visited pair: the whole list
+            // of each state; fl_prev / vprev hold the last step's new pairs
+            const long long all = sh.vnext[t] + (long long)fv;
+            sh.fl_prev[t] = fv;
+            sh.vprev[t] = sh.vnext[t];
+            sh.vstart[t] = 0;
+            sh.fl[t] = (unsigned long long)all;
+            sh.vnext[t] = all;
+        } else {
+            sh.fl_prev[t] = sh.fl[t];
+            sh.vprev[t] = sh.vstart[t];
+            sh.vstart[t] += (long long)sh.fl[t];
+            sh.fl[t] = fv;
+            sh.vnext[t] = sh.vstart[t] + (long long)fv;
+        }
     }
     if (t < p.n_groups) sh.mfv[t] = m0;
     if (g1 < p.n_groups) sh.mfv[g1] = m1;
@@ -1410,12 +1422,18 @@ constexpr unsigned long long kPrecheckMass = 4096;
 // CTA 0 also accumulates the query's statistics (`account`).
 __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared &sh, bool account) {
     __shared__ int s_plan;
-    long long total = 0;
-    for (int q = 0; q < p.S; q++) total += (long long)sh.fl[q];
-    const bool expand = total > 0 && (p.max_levels == 0 || j < p.max_levels);
+    const bool a2 = sh.flags[1] != 0;  // an Algorithm 2 step (CTA 0 alone)
+    long long total = 0, fresh = 0;
+    for (int q = 0; q < p.S; q++) {
+        total += (long long)sh.fl[q];
+        fresh += (long long)(a2 ? sh.fl_prev[q] : sh.fl[q]);
+    }
+    // Algorithm 1 stops when M = 0, Algorithm 2 when P stops changing: both
+    // when the last step found no new pair
+    const bool expand = fresh > 0 && (p.max_levels == 0 || j < p.max_levels);
     if (account && threadIdx.x == 0) {
-        sh.stats[kStVisited] += total;
-        if (total > 0 && j > 0) sh.stats[kStLevels] = j;
+        sh.stats[kStVisited] += fresh;
+        if (fresh > 0 && j > 0) sh.stats[kStLevels] = j;
         if (expand) {
             sh.stats[kStExpanded] += total;
             sh.stats[kStPushBytes] += (long long)sh.lvl[0];
@@ -1430,7 +1448,8 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
             mass += sh.mfv[g];
             pairs += sh.fl[sh.gq[g]];
         }
-        const bool pull = (double)mass * (double)p.alpha >
+        const bool pull = !a2 &&
+                          (double)mass * (double)p.alpha >
                               (double)sh.unnz[u] + (double)sh.urows[u] &&
                           (long long)pairs >= p.min_pull;
         sh.upull[u] = pull ? 1 : 0;
@@ -1472,8 +1491,8 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
             sh.stats[kStPushUnits] += npush;
             sh.stats[kStPullUnits] += npull;
         }
-        const bool solo = p.solo_mass >= 0 && npull == 0 &&
-                          mass <= (unsigned long long)p.solo_mass && acc <= p.solo_items;
+        const bool solo = a2 || (p.solo_mass >= 0 && npull == 0 &&
+                                 mass <= (unsigned long long)p.solo_mass && acc <= p.solo_items);
         s_plan = solo ? kPlanSolo : kPlanGrid;
         sh.flags[0] = mass > (unsigned long long)kPrecheckMass ? 1 : 0;
     }
@@ -1519,7 +1538,7 @@ __device__ __forceinline__ int gate_wait(const KParams &p, unsigned &seen) {
                 if (b != beat) {
                     beat = b;
                     t0 = now;
-                } else if (now - t0 > kBarrierTimeoutNs) {
+                } else if (now - t0 > p.wait_ns) {
                     set_status(p.c, (int32_t)RPQ_ERR_TIMEOUT);
                     break;
                 }
@@ -1588,7 +1607,7 @@ __device__ __forceinline__ bool park_wait(const KParams &p, unsigned long long e
                         ok = 0;
                         break;
                     }
-                    if (global_timer_ns() - t0 > kBarrierTimeoutNs) {
+                    if (global_timer_ns() - t0 > p.wait_ns) {
                         set_status(p.c, (int32_t)RPQ_ERR_TIMEOUT);
                         ok = 0;
                         break;
@@ -1994,7 +2013,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             p.F[1][i] = 0;
             p.F[2][i] = 0;
         }
-        if (!grid_barrier(p.c)) return;
+        if (!grid_barrier(p)) return;
     }
     unsigned seen = 0;   // gate releases seen (the same count on every CTA)
     bool grid = false;   // the current level runs on the whole grid
@@ -2061,6 +2080,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             // parked while CTA 0 runs levels alone
             const int cmd = gate_wait(p, seen);
             if (cmd != kGateLevel && cmd != kGateFinal) return;
+            if (p.test_leave && blockIdx.x == gridDim.x - 1) return;  // failure test only
             j = *(volatile int32_t *)&p.c->pub_level;
             level_join(p, j, sh);
             grid = true;
@@ -2124,11 +2144,11 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             // lists
             __syncthreads();
             const bool fits = measure_buffer(p, sh, sh.cv[0], (j + 1) % 3, s_acc);
-            const int r = grid_sync(p.c, !fits);
+            const int r = grid_sync(p, !fits);
             if (r < 0) return;
             if (r > 0) {
                 if (lead) measure_reset(p, sh, (j + 1) % 3);
-                if (!grid_barrier(p.c)) return;
+                if (!grid_barrier(p)) return;
                 // every CTA has left the barrier that saw the flag: clear it
                 // now (earlier, a CTA still waiting there could miss it); the
                 // other parity's bit is clear, the barrier just passed takes
@@ -2137,13 +2157,34 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
                 if (!sort_level(p, sh, j)) return;
                 measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
                               s_acc);
-                if (!grid_barrier(p.c)) return;
+                if (!grid_barrier(p)) return;
             }
         } else {
             __syncthreads();
-            if (!measure_buffer(p, sh, sh.cv[1], (j + 1) % 3, s_acc))
-                measure_level(p, sh, sh.cv[1], (j + 1) % 3, 0, 1, s_acc);
+            // the hybrid: level j+1 is an Algorithm 2 step while the visited
+            // set (after level j) holds fewer than alg2_until pairs
+            __shared__ int s_a2;
+            if (threadIdx.x == 0) {
+                bool a2 = false;
+                if (p.alg2_until > 0) {
+                    long long vis = 0;
+                    const Ctrs &C1 = sh.cv[1];
+                    for (int q = 0; q < p.S; q++)
+                        vis += sh.vnext[q] + (long long)C1.fl[((j + 1) % 3) * kMaxStates + q];
+                    a2 = vis < p.alg2_until;
+                }
+                s_a2 = a2 ? 1 : 0;
+            }
             __syncthreads();
+            if (s_a2) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_nd = 0;  // the buffer holds only the new pairs: unused
+                measure_level(p, sh, sh.cv[1], (j + 1) % 3, 0, 1, s_acc, true);
+            } else if (!measure_buffer(p, sh, sh.cv[1], (j + 1) % 3, s_acc)) {
+                measure_level(p, sh, sh.cv[1], (j + 1) % 3, 0, 1, s_acc);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) sh.flags[1] = s_a2;
             heartbeat(p);
             if (load_status(p.c) != 0) return;
         }
@@ -2172,7 +2213,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
     }
     if (!solo_end) {
         final_phase(p, &s_claim);
-        if (!grid_barrier(p.c)) return;
+        if (!grid_barrier(p)) return;
         final_write(p, &s_claim);
         clear_state(p, sh, false, f_live, j, (int)blockIdx.x, (int)gridDim.x);
     }
@@ -2407,7 +2448,7 @@ rpq_status get_launch_shape(int device, size_t smem, int *grid) {
 }
 
 rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long row_cap,
-                    long long chunk_cap, long long srow_cap) {
+                    long long chunk_cap, long long srow_cap, cudaStream_t st) {
     const int64_t W = ((int64_t)g->n + 63) / 64;
     const size_t bits = sizeof(uint64_t) * (size_t)S_cap * W;
     const size_t fl = sizeof(int32_t) * (size_t)S_cap * g->n;
@@ -2427,10 +2468,15 @@ rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long
              ws->cmap[k].alloc(sizeof(int32_t) * (size_t)chunk_cap) &&
              ws->srl[k].alloc(sizeof(int4) * (size_t)srow_cap);
     if (!ok) return fail(RPQ_ERR_OOM, "query workspace (%d states)", S_cap);
-    // the kernel expects P and F all-zero on entry and leaves them so
-    RPQ_CUDA_TRY(cudaMemset(ws->ctr.p, 0, sizeof(Counters)));
-    RPQ_CUDA_TRY(cudaMemset(ws->P.p, 0, bits));
-    for (int k = 0; k < 3; k++) RPQ_CUDA_TRY(cudaMemset(ws->F[k].p, 0, bits));
+    // the kernel expects P and F all-zero on entry and leaves them so.  The
+    // clears go on the query's stream and complete before the workspace is
+    // used: a plain cudaMemset would be ordered only on the legacy default
+    // stream, which the non-blocking streams of the slot engines do not wait
+    // for (a kernel there could see the memory's earlier contents)
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->ctr.p, 0, sizeof(Counters), st));
+    RPQ_CUDA_TRY(cudaMemsetAsync(ws->P.p, 0, bits, st));
+    for (int k = 0; k < 3; k++) RPQ_CUDA_TRY(cudaMemsetAsync(ws->F[k].p, 0, bits, st));
+    RPQ_CUDA_TRY(cudaStreamSynchronize(st));
     ws->staging_bytes = kResultOffset + sizeof(QueryResult);
     RPQ_CUDA_TRY(cudaHostAlloc(&ws->staging, ws->staging_bytes, cudaHostAllocMapped));
     memset(ws->staging, 0, ws->staging_bytes);
@@ -2444,7 +2490,7 @@ rpq_status ws_alloc(QueryWorkspace *ws, const rpq_graph *g, int S_cap, long long
 
 std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, long long row_need,
                                            long long chunk_need, long long srow_need,
-                                           rpq_status *st) {
+                                           rpq_status *st, cudaStream_t stream) {
     {
         std::lock_guard<std::mutex> lk(g->ws_mu);
         for (size_t i = 0; i < g->ws_free.size(); i++) {
@@ -2465,7 +2511,7 @@ std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, long long row_ne
     while (rc < row_need) rc *= 2;
     while (cc < chunk_need) cc *= 2;
     while (sc < srow_need) sc *= 2;
-    *st = ws_alloc(w.get(), g, S_cap, rc, cc, sc);
+    *st = ws_alloc(w.get(), g, S_cap, rc, cc, sc, stream);
     if (*st != RPQ_OK) return nullptr;
     return w;
 }
@@ -2652,6 +2698,20 @@ constexpr long long kSortPairs = 131072;
 constexpr int kSortBuffer = 1024;
 constexpr int32_t kSortVertices = 1 << 22;
 
+// Limit of the device waits (RPQ_WAIT_LIMIT_MS, default 4 s) and the
+// failure test's early exit of one CTA (RPQ_TEST_LEAVE_CTA=1).
+// The Algorithm 2 -> Algorithm 1 switch: the graph's setting
+// (rpq_graph_set_hybrid), RPQ_ALG2_SWITCH overrides.
+void hybrid_policy(const rpq_graph *g, KParams &p) {
+    p.alg2_until = std::max(0LL, (long long)env_float("RPQ_ALG2_SWITCH", (float)g->alg2_until));
+}
+
+void wait_policy(KParams &p) {
+    const float ms = env_float("RPQ_WAIT_LIMIT_MS", (float)(kBarrierTimeoutNs / 1000000ull));
+    p.wait_ns = (uint64_t)(std::max(1.0f, ms) * 1e6f);
+    p.test_leave = env_float("RPQ_TEST_LEAVE_CTA", 0.0f) != 0.0f ? 1 : 0;
+}
+
 void sort_policy(const rpq_graph *g, KParams &p) {
     const bool big = g->n >= kSortVertices;
     p.sort_min = (long long)env_float("RPQ_SORT_MIN", big ? (float)kSortPairs : 0.0f);
@@ -2779,7 +2839,7 @@ rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_
     rpq_status s = build_tables(g, a, &t);
     if (s != RPQ_OK) return s;
     std::unique_ptr<QueryWorkspace> ws =
-        ws_acquire(g, a.S, t.row_need, t.chunk_need, t.srow_need, &s);
+        ws_acquire(g, a.S, t.row_need, t.chunk_need, t.srow_need, &s, st);
     if (!ws) return s;
     uint8_t *hs = static_cast<uint8_t *>(ws->staging);
     KParams p{};
@@ -2831,6 +2891,8 @@ rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_
     p.solo_mass = (int32_t)env_float("RPQ_SOLO_MASS", (float)g->solo_mass);
     p.solo_items = (int32_t)env_float("RPQ_SOLO_ITEMS", (float)g->solo_items);
     sort_policy(g, p);
+    wait_policy(p);
+    hybrid_policy(g, p);
     p.sort_cnt = ws->sortc.as<uint32_t>();
     p.epoch = ++ws->epoch;
     p.clear_first = ws->dirty ? 1 : 0;
@@ -3038,6 +3100,13 @@ rpq_status autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas, const i
 }
 }  // namespace rpq
 
+extern "C" rpq_status rpq_graph_set_hybrid(rpq_graph *g, int64_t switch_pairs) {
+    rpq::clear_error();
+    if (!g || switch_pairs < 0) return rpq::fail(RPQ_ERR_INVALID, "bad argument");
+    g->alg2_until = switch_pairs;
+    return RPQ_OK;
+}
+
 extern "C" rpq_status rpq_graph_autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
                                          const int32_t *sources, float *alpha_out,
                                          int32_t *min_pull_out, int32_t *solo_mass_out,
@@ -3064,7 +3133,7 @@ uint32_t g_noalloc_epoch[64]; // launches on the scratch, per device
 // Device address of the scratch on `device` (which must be current), looked
 // up once per device; the barrier counters are cleared on that first call.
 // Also hands out the launch's epoch.
-rpq_status noalloc_scratch(int device, void **out, uint32_t *epoch) {
+rpq_status noalloc_scratch(int device, void **out, uint32_t *epoch, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (device < 0 || device >= 64) return fail(RPQ_ERR_CUDA, "device id %d", device);
     if (!g_noalloc_ptr[device]) {
@@ -3072,7 +3141,9 @@ rpq_status noalloc_scratch(int device, void **out, uint32_t *epoch) {
         const cudaError_t e = cudaGetSymbolAddress(&ptr, rpq_noalloc_scratch);
         if (e != cudaSuccess || !ptr)
             return fail(RPQ_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        RPQ_CUDA_TRY(cudaMemset(ptr, 0, sizeof(Counters)));
+        // on the caller's stream, ordered before the launch that follows
+        RPQ_CUDA_TRY(cudaMemsetAsync(ptr, 0, sizeof(Counters), st));
+        RPQ_CUDA_TRY(cudaStreamSynchronize(st));
         g_noalloc_ptr[device] = ptr;
     }
     *out = g_noalloc_ptr[device];
@@ -3152,10 +3223,10 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
                     off, (unsigned long long)RPQ_NOALLOC_SCRATCH_BYTES);
     void *base_v = nullptr;
     uint32_t epoch = 0;
-    s = noalloc_scratch(dev, &base_v, &epoch);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = noalloc_scratch(dev, &base_v, &epoch, st);
     if (s != RPQ_OK) return s;
     uint8_t *base = static_cast<uint8_t *>(base_v);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     RPQ_CUDA_TRY(cudaMemcpyAsync(base + x_tab, host_tables.data(), std::max<size_t>(toff, 1),
                                  cudaMemcpyHostToDevice, st));
 
@@ -3178,6 +3249,8 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     p.solo_mass = g->solo_mass;
     p.solo_items = g->solo_items;
     sort_policy(g, p);
+    wait_policy(p);
+    hybrid_policy(g, p);
     p.sort_cnt = reinterpret_cast<uint32_t *>(base + x_sort);
     // the scratch layout moves with the automaton's size: clear P / F first
     p.clear_first = 1;

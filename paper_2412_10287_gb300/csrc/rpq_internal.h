@@ -26,13 +26,23 @@ void clear_error();
 const char *rpq_last_error_str();  // this thread's last message
 
 // ------------------------------------------------------------- allocator --
-void *dev_alloc(size_t bytes);  // nullptr on failure
-void dev_free(void *p);
+// The device allocator (rpq_set_allocator): a pair of callbacks and their
+// context, or all null for cudaMalloc / cudaFree.
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+// Allocates with the current allocator and reports which one it was, so
+// that the memory goes back to that allocator even after a change.
+void *dev_alloc(size_t bytes, Allocator *used);  // nullptr on failure
+void dev_free(void *p, const Allocator &used);
 
 // RAII device buffer from the library allocator.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    Allocator by;  // the allocator that made p
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
@@ -40,12 +50,12 @@ struct DevBuf {
     bool alloc(size_t b) {
         reset();
         if (b == 0) b = 16;
-        p = dev_alloc(b);
+        p = dev_alloc(b, &by);
         bytes = p ? b : 0;
         return p != nullptr;
     }
     void reset() {
-        if (p) dev_free(p);
+        if (p) dev_free(p, by);
         p = nullptr;
         bytes = 0;
     }

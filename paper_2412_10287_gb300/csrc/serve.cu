@@ -95,6 +95,10 @@ struct rpq_server {
     int64_t budget = 0;          // 0 = no limit
     int64_t inflight_bytes = 0, peak_bytes = 0;
     int inflight_n = 0, peak_inflight = 0;
+    // engine 0: queries in flight at most, lowered after an allocation
+    // failure (back-off) and raised again as queries complete
+    int slot_cap = 0;
+    int64_t oom_retries = 0;
     // statistics
     int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, level_steps = 0;
     std::vector<double> latency_ms;
@@ -407,7 +411,8 @@ void slot_worker_main(rpq_server *s) {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] {
                 return s->stop ||
-                       (!s->queue.empty() && fits_budget(s, query_bytes(s, s->queue.front().a)));
+                       (!s->queue.empty() && s->inflight_n < s->slot_cap &&
+                        fits_budget(s, query_bytes(s, s->queue.front().a)));
             });
             if (s->stop) break;
             q = std::move(s->queue.front());
@@ -425,8 +430,21 @@ void slot_worker_main(rpq_server *s) {
         if (r == RPQ_OK) ans.assign(buf.begin(), buf.begin() + cnt);
         {
             std::lock_guard<std::mutex> lk(s->mu);
+            if (r == RPQ_ERR_OOM && s->inflight_n > 1) {
+                // device memory ran out beside the other queries in flight:
+                // admit fewer at once and run this query again when one ends
+                retire_account(s, need);
+                s->admitted--;
+                s->slot_cap = std::max(1, s->inflight_n);
+                s->oom_retries++;
+                s->queue.push_front(std::move(q));
+                s->cv.notify_all();
+                continue;
+            }
             finish_ticket(s, q.ticket, r, std::move(ans), q.t_submit);
             retire_account(s, need);
+            if (r == RPQ_OK && s->slot_cap < s->lanes_max && s->completed % 16 == 0)
+                s->slot_cap++;
             // the levels this query expanded: its non-empty levels after
             // level 0, plus level 0 (the last expansion finds nothing)
             if (r == RPQ_OK) s->level_steps += qs.levels + 1;
@@ -463,6 +481,7 @@ extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_confi
         s->max_levels = c.max_levels;
         s->queue_cap = c.queue_capacity > 0 ? (size_t)c.queue_capacity : 65536;
         s->budget = c.memory_budget;
+        s->slot_cap = slots;
         rpq_server *raw = s.get();
         for (int k = 0; k < slots; k++) s->slot_workers.emplace_back(slot_worker_main, raw);
         *out = s.release();
@@ -615,6 +634,7 @@ extern "C" rpq_status rpq_serve_stats_get(rpq_server *s, struct rpq_serve_stats 
     r.level_steps = s->level_steps;
     r.peak_in_flight = s->peak_inflight;
     r.peak_bytes = s->peak_bytes;
+    r.oom_retries = s->oom_retries;
     if (!s->latency_ms.empty()) {
         std::vector<double> v = s->latency_ms;
         std::sort(v.begin(), v.end());

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "RPQ_OK", 1: "RPQ_ERR_INVALID", 2: "RPQ_ERR_PARSE", 3: "RPQ_E
 # Every symbol include/rpq.h declares.
 EXPORTED = (
     "rpq_set_allocator", "rpq_graph_load", "rpq_graph_free", "rpq_graph_info", "rpq_graph_export",
-    "rpq_graph_autotune",
+    "rpq_graph_autotune", "rpq_graph_set_hybrid",
     "rpq_nfa_compile", "rpq_nfa_from_transitions", "rpq_nfa_free", "rpq_nfa_info",
     "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_last_answer",
     "rpq_query_noalloc",
@@ -72,7 +72,8 @@ class RpqServeStats(ctypes.Structure):
                 ("level_steps", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("elapsed_s", ctypes.c_double), ("qps", ctypes.c_double),
-                ("peak_in_flight", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
+                ("peak_in_flight", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("oom_retries", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +100,7 @@ def lib():
             "rpq_graph_info": [p, i32, p, p, p],
             "rpq_graph_export": [p, i32, i32, p, p, i64],
             "rpq_graph_autotune": [p, i32, p, p, p, p, p, p],
+            "rpq_graph_set_hybrid": [p, i64],
             "rpq_nfa_compile": [ctypes.c_char_p, i32, pp],
             "rpq_nfa_from_transitions": [i32, i32, i32, p, p, p, i32, p, i32, p, pp],
             "rpq_nfa_info": [p, p, p, p],
@@ -261,6 +263,12 @@ def rpq_graph_export(g: Graph, label: int, inverse: bool):
     nbr = np.zeros(max(int(off[-1]), 1), np.int32)
     _check(lib().rpq_graph_export(g.h, label, int(inverse), _ptr(off), _ptr(nbr), nbr.size))
     return off, nbr[: int(off[-1])]
+
+
+def rpq_graph_set_hybrid(g: Graph, switch_pairs: int):
+    """Algorithm 2 while fewer than ``switch_pairs`` pairs are visited, then
+    Algorithm 1 (section 5.1's hybrid); 0 turns it off."""
+    _check(lib().rpq_graph_set_hybrid(g.h, int(switch_pairs)))
 
 
 def rpq_graph_autotune(g: Graph, nfas, sources, stream=None):

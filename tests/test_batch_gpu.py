@@ -144,3 +144,26 @@ def test_batch_with_discovery_buffer_overflow(cap, monkeypatch):
     for i in range(96):
         exp = og.ssr(oracle_compile(texts[i % len(texts)], 4), srcs[i])["answer"]
         assert got[i].tolist() == exp.tolist(), i
+
+
+def test_fresh_workspaces_on_reused_memory(engine):
+    """Device memory freed by an earlier graph comes back, with its old
+    contents, as the workspaces of a new graph; those are first used on the
+    slot engine's non-blocking streams.  Their clears must be ordered before
+    that use: every answer equals the oracle's."""
+    junk = W.rmat_graph(18, 1 << 22, 4, seed=43)  # ~50 MB of non-zero ids, then freed
+    jg = load(junk)
+    del jg
+    import gc
+
+    gc.collect()
+    g = W.rmat_graph(15, 1 << 19, 4, seed=44)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    texts = ["0*", "(0|^1)*/2", "1/(0|2)*", "(0/1)*", "^3/(1|2)+", "(0|1|2|3)*"]
+    srcs = W.below(45, 1, 48, g.n).tolist()
+    nfas = [R.rpq_nfa_compile(texts[i % len(texts)], 4) for i in range(48)]
+    got = R.rpq_query_batch(gg, nfas, srcs)
+    for i in range(48):
+        exp = og.ssr(oracle_compile(texts[i % len(texts)], 4), srcs[i])["answer"]
+        assert got[i].tolist() == exp.tolist(), i

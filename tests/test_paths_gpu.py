@@ -250,3 +250,61 @@ def test_witness_long_chain_and_capacity():
     assert st == R.RPQ_ERR_CAPACITY and ln.value == m - 1
     assert R.rpq_query_witness(gg, R.rpq_nfa_compile("^0", 1), [5], 4)[1].tolist() == [1]
     assert R.rpq_query_witness(gg, nfa, [5], 4) is None  # not reachable forwards
+
+
+# ------------------------------------- Algorithm 2 -> Algorithm 1 hybrid --
+# Section 5.1: Algorithm 2 (every step expands the whole visited set, no
+# traversal matrix M) while the visited set is small, then Algorithm 1.
+# The sets P_k are the same either way (section 4), so answers, levels and
+# visited counts equal the oracle's; with Algorithm 2 throughout, the
+# expanded-pair counter is the sum of |P_j| over the expanded levels j.
+
+@pytest.mark.parametrize("switch", [1 << 40, 100, 7])
+def test_hybrid_tiny_random(switch):
+    for seed in range(60):
+        g = W.tiny_graph(seed + 9100, max_n=12, max_m=30)
+        S, trans, starts, finals = W.tiny_automaton(seed + 9200, g.n_labels, max_states=5,
+                                                    max_trans=10)
+        og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+        gg = load(g)
+        R.rpq_graph_set_hybrid(gg, switch)
+        dn = R.rpq_nfa_from_transitions(S, g.n_labels, trans, starts, finals)
+        on = Nfa(S, g.n_labels, trans, starts, finals)
+        src = seed % g.n
+        for k in (0, 2):
+            exp = og.ssr(on, src, k, level_cap=64)
+            got, st = R.rpq_query(gg, dn, src, k, with_stats=True)
+            assert got.tolist() == exp["answer"].tolist(), (seed, k, switch)
+            c = exp["counters"]
+            assert (st["levels"], st["visited_pairs"]) == (c["levels"], c["visited"]), (seed, k)
+            assert st["expanded_pairs"] >= c["expanded"]
+            if switch == 1 << 40 and k == 0:
+                sizes = np.cumsum(exp["level_sizes"][: c["levels"] + 1])
+                assert st["expanded_pairs"] == int(sizes.sum()), (seed, sizes)
+        og.close()
+
+
+def test_hybrid_rmat_switches_to_algorithm_1(rmat14):
+    g, gg, og = rmat14
+    srcs = W.below(95, 1, 4, g.n).tolist()
+    R.rpq_graph_set_hybrid(gg, 100)
+    try:
+        for text in TEXTS:
+            on = oracle_compile(text, 4)
+            nfa = R.rpq_nfa_compile(text, 4)
+            for s in srcs:
+                # regex automata differ between the two sides (minimised DFA
+                # here, Thompson NFA in the oracle), so the counters are
+                # compared with Algorithm 1 on the same DFA
+                exp = og.ssr(on, s)
+                got, st = R.rpq_query(gg, nfa, s, with_stats=True)
+                assert got.tolist() == exp["answer"].tolist(), (text, s)
+                R.rpq_graph_set_hybrid(gg, 0)
+                _, st1 = R.rpq_query(gg, nfa, s, with_stats=True)
+                R.rpq_graph_set_hybrid(gg, 100)
+                assert st["levels"] == st1["levels"], (text, s)
+                assert st["visited_pairs"] == st1["visited_pairs"], (text, s)
+                assert st["expanded_pairs"] >= st1["expanded_pairs"], (text, s)
+            assert R.rpq_query_multi(gg, nfa, srcs).tolist() == og.query(on, srcs)["answer"].tolist()
+    finally:
+        R.rpq_graph_set_hybrid(gg, 0)
