@@ -72,6 +72,9 @@ def parse():
                     help="profiling case: run this regex once for warm-up and once more "
                          "(with --source) on the workload's graph, print its counters, exit")
     ap.add_argument("--source", type=int, default=0)
+    ap.add_argument("--kb-size", default=None, metavar="N,M",
+                    help="with --one-query: a knowledge-base graph of N vertices and M edges "
+                         "(same generator and seed as kb20m) instead of the workload's graph")
     ap.add_argument("--profile-sample", type=int, default=0, metavar="N",
                     help="profiling case: run the workload's queries once, then again only "
                          "the N with the most algorithmic bytes (the launches to capture), "
@@ -797,7 +800,11 @@ def main():
         from paper_2412_10287_gb300 import rpq as R
         from paper_2412_10287_gb300 import workloads as W
 
-        g = W.config3_graph() if args.workload == "kb20m" else W.config2_graph()
+        if args.kb_size:
+            n_, m_ = (int(x) for x in args.kb_size.split(","))
+            g = W.config3_graph(n_, m_)
+        else:
+            g = W.config3_graph() if args.workload == "kb20m" else W.config2_graph()
         gg = R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
         nfa = R.rpq_nfa_compile(args.one_query, g.n_labels)
         for _ in range(2):

@@ -192,6 +192,9 @@ struct KParams {
     // holds fewer than alg2_until pairs, then Algorithm 1 (the hybrid switch
     // of section 5.1); 0 = Algorithm 1 throughout
     long long alg2_until;
+    // push levels with more edge mass than this read the visited word before
+    // each atomicOr (most of their targets are already visited)
+    long long precheck_mass;
     Counters *c;
     // output
     int32_t *out_list;
@@ -516,9 +519,12 @@ __shared__ uint8_t s_dq[kDisc];  // their states
 __shared__ int s_nd;             // pairs discovered by this CTA in the level
 
 // Lanes with found[r] have discovered the new pair (q2, w[r]) of the next
-// level: appended to the visited list of q2 (one reservation for the warp)
-// and to the CTA's discovery buffer, and, on grid levels, its frontier bit
-// set.  The rows the pair will expand are measured after the level
+// level: kept in the CTA's discovery buffer (a shared-memory counter gives
+// the position: no global round trip) and, on grid levels, its frontier bit
+// set.  The buffer goes to the visited lists when the CTA's expansion ends
+// (flush_discoveries: one reservation per state and CTA); pairs past the
+// buffer's end are appended to the list of q2 at once (one reservation for
+// the warp).  The rows the pair will expand are measured after the level
 // (measure_buffer), with many lookups in flight instead of one chain per
 // discovery.  q2 warp-uniform; all 32 lanes call.
 template <int kB>
@@ -534,14 +540,17 @@ __device__ __forceinline__ void warp_discover_batch(const KParams &p, const Leve
     }
     if (!total) return;
     const unsigned lane = lane_id();
-    unsigned long long base = 0;
     int pos = 0;
-    if (lane == 0) {
-        base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)total);
-        pos = atomicAdd(&s_nd, total);
-    }
-    base = __shfl_sync(kFull, base, 0);
+    if (lane == 0) pos = atomicAdd(&s_nd, total);
     pos = __shfl_sync(kFull, pos, 0);
+    // entries k >= fit do not fit the buffer: listed directly
+    const int fit = max(0, min(total, kDisc - pos));
+    unsigned long long base = 0;
+    if (fit < total) {  // warp-uniform
+        if (lane == 0)
+            base = atomicAdd(&L.C->fl[L.slot * kMaxStates + q2], (unsigned long long)(total - fit));
+        base = __shfl_sync(kFull, base, 0);
+    }
     int32_t *lst = L.VL + (size_t)q2 * p.n + L.vnext[q2];
     uint64_t *Fq = L.F ? L.F + (size_t)q2 * p.W : nullptr;
     int run = 0;
@@ -549,10 +558,11 @@ __device__ __forceinline__ void warp_discover_batch(const KParams &p, const Leve
     for (int r = 0; r < kB; r++) {
         if (found[r]) {
             const int k = run + __popc(m[r] & lanemask_lt());
-            lst[base + k] = w[r];
-            if (pos + k < kDisc) {
+            if (k < fit) {
                 s_dw[pos + k] = w[r];
                 s_dq[pos + k] = (uint8_t)q2;
+            } else {
+                lst[base + (k - fit)] = w[r];
             }
             if (Fq)
                 atomicOr((unsigned long long *)(Fq + ((uint32_t)w[r] >> 6)), 1ull << (w[r] & 63));
@@ -567,6 +577,34 @@ __device__ __forceinline__ void warp_discover(const KParams &p, const LevelCtx &
     const bool f[1] = {found};
     const int32_t x[1] = {w};
     warp_discover_batch<1>(p, L, f, q2, x);
+}
+
+// End of a CTA's expansion (all its threads): the buffered discoveries go to
+// the visited lists of the level in counter slot `slot` of C, after one
+// reservation per state.  The buffer stays as it is for measure_buffer.
+__device__ void flush_discoveries(const KParams &p, const Shared &sh, const Ctrs &C, int slot) {
+    __shared__ unsigned s_cnt[kMaxStates];
+    __shared__ unsigned long long s_base[kMaxStates];
+    __syncthreads();
+    const int nd = min(s_nd, kDisc);
+    if (nd == 0) return;  // CTA-uniform
+    if (threadIdx.x < kMaxStates) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd; i += kThreads) atomicAdd(&s_cnt[s_dq[i]], 1u);
+    __syncthreads();
+    if (threadIdx.x < p.S) {
+        const unsigned c = s_cnt[threadIdx.x];
+        s_base[threadIdx.x] =
+            c ? atomicAdd(&C.fl[slot * kMaxStates + threadIdx.x], (unsigned long long)c) : 0ull;
+        s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd; i += kThreads) {
+        const int q = s_dq[i];
+        const unsigned k = atomicAdd(&s_cnt[q], 1u);
+        p.VL[(size_t)q * p.n + sh.vnext[q] + s_base[q] + k] = s_dw[i];
+    }
+    __syncthreads();
 }
 
 // Rows in group g of new pairs (q, w[r]) of the level in counter slot
@@ -1494,7 +1532,7 @@ __device__ __forceinline__ int level_plan(const KParams &p, int j, const Shared 
         const bool solo = a2 || (p.solo_mass >= 0 && npull == 0 &&
                                  mass <= (unsigned long long)p.solo_mass && acc <= p.solo_items);
         s_plan = solo ? kPlanSolo : kPlanGrid;
-        sh.flags[0] = mass > (unsigned long long)kPrecheckMass ? 1 : 0;
+        sh.flags[0] = (long long)mass > p.precheck_mass ? 1 : 0;
     }
     __syncthreads();
     const int plan = s_plan;
@@ -2062,7 +2100,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
                 }
             }
         }
-        __syncthreads();
+        flush_discoveries(p, sh, sh.cv[1], 0);
         if (!measure_buffer(p, sh, sh.cv[1], 0, s_acc))
             measure_level(p, sh, sh.cv[1], 0, 0, 1, s_acc);
         __syncthreads();
@@ -2142,7 +2180,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             // every CTA measures what it discovered, from its buffer; if a
             // buffer overflowed, the grid measures the level again from the
             // lists
-            __syncthreads();
+            flush_discoveries(p, sh, sh.cv[0], (j + 1) % 3);
             const bool fits = measure_buffer(p, sh, sh.cv[0], (j + 1) % 3, s_acc);
             const int r = grid_sync(p, !fits);
             if (r < 0) return;
@@ -2160,7 +2198,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
                 if (!grid_barrier(p)) return;
             }
         } else {
-            __syncthreads();
+            flush_discoveries(p, sh, sh.cv[1], (j + 1) % 3);
             // the hybrid: level j+1 is an Algorithm 2 step while the visited
             // set (after level j) holds fewer than alg2_until pairs
             __shared__ int s_a2;
@@ -2706,6 +2744,10 @@ void hybrid_policy(const rpq_graph *g, KParams &p) {
     p.alg2_until = std::max(0LL, (long long)env_float("RPQ_ALG2_SWITCH", (float)g->alg2_until));
 }
 
+void precheck_policy(KParams &p) {
+    p.precheck_mass = (long long)env_float("RPQ_PRECHECK_MASS", (float)kPrecheckMass);
+}
+
 void wait_policy(KParams &p) {
     const float ms = env_float("RPQ_WAIT_LIMIT_MS", (float)(kBarrierTimeoutNs / 1000000ull));
     p.wait_ns = (uint64_t)(std::max(1.0f, ms) * 1e6f);
@@ -2893,6 +2935,7 @@ rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_
     sort_policy(g, p);
     wait_policy(p);
     hybrid_policy(g, p);
+    precheck_policy(p);
     p.sort_cnt = ws->sortc.as<uint32_t>();
     p.epoch = ++ws->epoch;
     p.clear_first = ws->dirty ? 1 : 0;
@@ -3251,6 +3294,7 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     sort_policy(g, p);
     wait_policy(p);
     hybrid_policy(g, p);
+    precheck_policy(p);
     p.sort_cnt = reinterpret_cast<uint32_t *>(base + x_sort);
     // the scratch layout moves with the automaton's size: clear P / F first
     p.clear_first = 1;
