@@ -436,6 +436,12 @@ def run_batch(args, R, torch, g=None, gg=None):
     g = g or W.config2_graph()
     w = W.config4(g, 256)
     gg = gg or R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
+    # the lane engine's tuning (inline row length, pull divisor) on a sample
+    # drawn apart from the timed queries: one automaton from 64 sources of
+    # another seed (the shared-automaton batches lanes serve)
+    tune_srcs = W.below(33, 1, 64, g.n).tolist()
+    lane_hub, lane_pull = R.rpq_graph_autotune_batch(
+        gg, [R.rpq_nfa_compile("0*", g.n_labels)] * 64, tune_srcs)
     nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in w.queries]
     srcs = [q.source for q in w.queries]
     states = [n.info()[0] for n in nfas]
@@ -486,11 +492,14 @@ def run_batch(args, R, torch, g=None, gg=None):
     shared = [R.rpq_nfa_compile("0*", g.n_labels)] * len(srcs)
     sh_handles = (ctypes.c_void_p * len(shared))(*[x.h.value for x in shared])
     for label, env, jobs in (("mixed_on_lanes", "lanes", None),
+                             ("mixed_on_lanes_push_only", "lanes_push", None),
                              ("shared_automaton_lanes", None, "shared"),
                              ("shared_automaton_sequential", None, "shared_seq")):
         old_env = os.environ.get("RPQ_BATCH_ENGINE")
         if env:
-            os.environ["RPQ_BATCH_ENGINE"] = env
+            os.environ["RPQ_BATCH_ENGINE"] = "lanes"
+        if env == "lanes_push":
+            os.environ["RPQ_LANE_PULL_DIV"] = "0"
         try:
             if jobs is None:
                 fn = batch_once
@@ -520,6 +529,7 @@ def run_batch(args, R, torch, g=None, gg=None):
                 ts_.append(time.perf_counter() - t0)
             extra[label] = len(srcs) * args.steps / sum(ts_)
         finally:
+            os.environ.pop("RPQ_LANE_PULL_DIV", None)
             if env:
                 if old_env is None:
                     os.environ.pop("RPQ_BATCH_ENGINE", None)
@@ -531,6 +541,8 @@ def run_batch(args, R, torch, g=None, gg=None):
             "sequential_single_queries_per_s": qs, "batch_speedup": qb / qs,
             "engine": os.environ.get("RPQ_BATCH_ENGINE", "auto (slots for mixed automata)"),
             "other_engines_queries_per_s": extra,
+            "lane_autotuned": {"lane_hub": lane_hub, "pull_div": lane_pull,
+                               "sample": "one automaton (0*) from 64 sources of another seed"},
             "answer_vertices_per_step": int(total), "gpu_launches": batch_launches,
             "l2": "flushed between steps (256 MiB write)"}
 
@@ -719,6 +731,68 @@ def run_rmat20_extra(args, R, torch, g, gg):
             "gpu_launches": m["launches"]}
 
 
+RARE_MAX = 200_000  # edges: labels at or below this count as rare for the rare-first plan
+
+
+def rare_queries(g, count=48, seed=7):
+    """Queries whose last label is rare: a/b*/c and a/(b|^d)*/c with a, b, d
+    among the 10 most frequent labels and c among the labels with at most
+    RARE_MAX edges (the long tail of the Zipf label distribution)."""
+    from paper_2412_10287_gb300 import workloads as W
+
+    counts = np.bincount(g.lab, minlength=g.n_labels)
+    order = np.argsort(-counts)
+    freq = order[:10]
+    tail = np.flatnonzero((counts > 0) & (counts <= RARE_MAX))
+    if tail.size == 0:
+        return []
+    r = W.below(seed, 1, 5 * count, 1 << 30)
+    deg = np.bincount(g.src, minlength=g.n) + np.bincount(g.dst, minlength=g.n)
+    cand = np.flatnonzero(deg > 0)
+    qs = []
+    for i in range(count):
+        a, b, d = (int(freq[r[5 * i + k] % freq.size]) for k in range(3))
+        c = int(tail[r[5 * i + 3] % tail.size])
+        text = f"{a}/{b}*/{c}" if i % 2 == 0 else f"{a}/({b}|^{d})*/{c}"
+        qs.append(W.Query(text, int(cand[r[5 * i + 4] % cand.size]), "rare-last"))
+    return qs
+
+
+def run_rare_plan(args, R, torch, w, gg):
+    """Rare label first against the plain search, on queries whose last
+    label is rare and on the workload's own queries; answers compared."""
+    g = w.graph
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(qs, nfas, plan):
+        R.rpq_graph_set_rare_plan(gg, RARE_MAX if plan else 0)
+        answers = []
+        for rep_ in range(2):  # warm-up pass, then the timed one
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cnts = [R.rpq_query(gg, nfa, q.source, out=out, stream=stream)
+                    for nfa, q in zip(nfas, qs)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+        for nfa, q in zip(nfas, qs[:16]):
+            answers.append(R.rpq_query(gg, nfa, q.source).tolist())
+        R.rpq_graph_set_rare_plan(gg, 0)
+        return len(qs) / (e0.elapsed_time(e1) / 1000.0), cnts, answers
+
+    res = {"rare_max_edges": RARE_MAX}
+    for name, qs in (("rare_last_label", rare_queries(g)), ("workload", w.queries)):
+        if not qs:
+            continue
+        nfas = [R.rpq_nfa_compile(q.regex, g.n_labels) for q in qs]
+        q0, c0, a0 = timed(qs, nfas, False)
+        q1, c1, a1 = timed(qs, nfas, True)
+        res[name] = {"queries": len(qs), "plain_queries_per_s": q0, "rare_first_queries_per_s": q1,
+                     "speedup": q1 / q0, "answers_equal": c0 == c1 and a0 == a1}
+    return res
+
+
 def run_extras(args, R, torch):
     """rmat20, batch and serve figures on the R-MAT scale-20 graph."""
     from paper_2412_10287_gb300 import workloads as W
@@ -902,8 +976,11 @@ def main():
 
     extras = None
     if ws == 1 and not args.no_extras:
+        rare = run_rare_plan(args, R, torch, w, gg) if name == "kb20m" else None
         gg.close()  # the R-MAT graph takes its place on the device
         extras = run_extras(args, R, torch)
+        if rare:
+            extras["rare_first"] = rare
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -141,6 +141,38 @@ rpq_status rpq_graph_autotune(rpq_graph *g, int32_t n, const rpq_nfa *const *nfa
  * overrides). */
 rpq_status rpq_graph_set_hybrid(rpq_graph *g, int64_t switch_pairs);
 
+/* Rare label first, an evaluation order (the paper finds its BFS slowest
+ * where it does not exploit rare labels or evaluation order, sections
+ * 5.4-5.5, and names rare labels as future work, section 6).  For rpq_query
+ * calls whose automaton reads, on every accepting path, a label direction
+ * with at most `max_edges` edges (the rarest such one that some transition
+ * not leaving a start state reads is taken): (1) a
+ * backward search, the reversed automaton without that label (section 4,
+ * SSR of N^-) from the vertices with such an edge, finds the (state,
+ * vertex) pairs that can still reach one; (2) the forward search of
+ * Algorithm 1 on a two-copy automaton (before / after reading the label)
+ * never enters a pair before the label that the backward search did not
+ * find.  The answer never changes; the counters are the forward search's.
+ * 0 (the default) turns it off; RPQ_RARE_MAX overrides.  Automata of more
+ * than 32 states are run as usual. */
+rpq_status rpq_graph_set_rare_plan(rpq_graph *g, int64_t max_edges);
+
+/* Autotuner of the bit-lane engine of rpq_query_batch (the push/pull
+ * threshold and tile shape of the batched form): runs the n sample queries
+ * (nfas[i] from sources[i]) on the lane kernel, in groups of up to 256, under
+ * every pair of (a) the inline row length, the edges of a (vertex, label
+ * direction) row a warp pushes itself before the rest of the row is cut into
+ * 128-edge chunks for other warps, in {32, 64, 128, 256}, and (b) the pull
+ * divisor: a level pulls (every vertex ORs the frontier lanes of its
+ * in-neighbours until the lanes it still misses are found) when the
+ * frontier holds more than n / divisor vertices, divisor in {0 (never), 2,
+ * 4, 8, 16}.  Keeps the fastest by device time for later batches on g
+ * (RPQ_LANE_HUB and RPQ_LANE_PULL_DIV override) and reports it; out pointers
+ * may be NULL.  Answers never depend on the setting. */
+rpq_status rpq_graph_autotune_batch(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
+                                    const int32_t *sources, int32_t *lane_hub_out,
+                                    int32_t *pull_div_out, void *stream);
+
 /* ---------------------------------------------------------- automaton -- */
 
 /* Compiles a regular expression over labels and inverse labels into a
@@ -369,8 +401,10 @@ typedef struct rpq_serve_stats {
  * bits in the four lane arrays, 4 x S x n bits (the lane arrays themselves
  * are allocated whole at creation, sized by max_lanes and max_states).  A
  * query that could never fit is refused at submission with RPQ_ERR_OOM.
- * Engine 0 also sizes each query's share of the SMs by the load: a query
- * admitted alone, with nothing queued, runs on the whole grid.  When a
+ * Engine 0 also sizes each query's share of the SMs by the queue at
+ * admission: a query that finds k - 1 others waiting runs on 1/k of the grid
+ * (at most 1/max_lanes), one that finds the queue empty on half of it
+ * (RPQ_SERVE_IDLE_DIV changes that divisor).  When a
  * query's device allocation fails while other queries are in flight, engine
  * 0 puts it back at the head of the queue and admits fewer queries at once
  * (raised again as queries complete); a query that fails alone completes

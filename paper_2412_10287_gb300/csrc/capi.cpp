@@ -234,8 +234,13 @@ extern "C" rpq_status rpq_query(const rpq_graph *g, const rpq_nfa *nfa, int32_t 
     int64_t count = 0;
     // a host answer (or none asked for) goes through the thread's pinned
     // buffer, where rpq_last_answer finds it
-    rpq_status s = run_query(gm, nfa->a, source, max_levels, dev ? out_vertices : nullptr, capacity,
-                             nullptr, dev ? nullptr : out_vertices, stats, &count, stream, !dev);
+    bool rare = false;
+    rpq_status s = run_query_rare(gm, nfa->a, source, max_levels, dev ? out_vertices : nullptr,
+                                  capacity, dev ? nullptr : out_vertices, stats, &count, stream,
+                                  !dev, &rare);
+    if (!rare && s == RPQ_OK)
+        s = run_query(gm, nfa->a, source, max_levels, dev ? out_vertices : nullptr, capacity,
+                      nullptr, dev ? nullptr : out_vertices, stats, &count, stream, !dev);
     if (s != RPQ_OK) return s;
     *out_count = count;
     if (count > capacity)

@@ -423,14 +423,22 @@ rpq_status build_side(rpq_graph *g, bool csc, int32_t *lab, int32_t *maj, int32_
                                      cudaMemcpyDeviceToHost, st));
         RPQ_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    // formats
+    // formats: dense offsets (n + 1) when at least n/16 rows are non-empty,
+    // when n is small, or when the label holds at least dense_edges edges,
+    // by default n/16 (a row is then found in one lookup instead of the
+    // bucket index's three; the offsets cost 4 (n + 1) bytes per direction,
+    // at most 64 bytes per edge of such a label); hypersparse otherwise.
+    // RPQ_DENSE_EDGES overrides the edge threshold (0: rows only).
+    const char *de = getenv("RPQ_DENSE_EDGES");
+    const int64_t dense_edges = de ? (int64_t)atoll(de) : std::max<int64_t>(1, n / 16);
     int64_t dense_words = 0, hyper_rows_total = 0, hyper_off_total = 0, bucket_total = 0;
     std::vector<int32_t> fmt(L), bbits(L, 0);
     for (int32_t a = 0; a < L; a++) {
         const int64_t nnz = start[a + 1] - start[a];
         if (nnz >= (int64_t(1) << 31)) return fail(RPQ_ERR_INVALID, "label %d has >= 2^31 edges", a);
         if (nnz == 0) fmt[a] = ADJ_EMPTY;
-        else if (rows[a] * 16 >= (int64_t)n || n <= 65536) fmt[a] = ADJ_DENSE;
+        else if (rows[a] * 16 >= (int64_t)n || n <= 65536 || (dense_edges > 0 && nnz >= dense_edges))
+            fmt[a] = ADJ_DENSE;
         else fmt[a] = ADJ_HYPER;
         if (fmt[a] == ADJ_DENSE) dense_words += (int64_t)n + 1;
         if (fmt[a] == ADJ_HYPER) {

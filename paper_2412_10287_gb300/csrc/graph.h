@@ -48,6 +48,12 @@ struct rpq_graph {
     int32_t solo_items = 256;
     // Algorithm 2 while the visited set is smaller than this (0: never)
     int64_t alg2_until = 0;
+    // single queries whose accepted words all read a label direction with at
+    // most this many edges run rare label first (rare.cu; 0: never)
+    int64_t rare_max = 0;
+    // lane engine tuning (rpq_graph_autotune_batch)
+    int32_t lane_hub = 128;
+    int32_t lane_pull_div = 0;
 
     std::mutex ws_mu;
     std::vector<std::unique_ptr<rpq::WorkspaceBase>> ws_free;

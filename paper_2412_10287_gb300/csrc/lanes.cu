@@ -11,7 +11,11 @@
 //           direction d:  X_{d,k2}[v] = OR_k M[v][k] & T[d][k][k2]  (the
 //           aggregate-first order (N^a)^T x M, section 4), then for every
 //           w in row v of G^d:  NX[w][k2] |= X & ~P[w][k2]  (atomicOr).
-//           Rows longer than kLaneHub are finished in chunks by other warps.
+//           Rows longer than p.lane_hub edges are finished in chunks by
+//           other warps.  When the frontier holds more than n / p.pull_div
+//           vertices the level pulls instead: for every vertex w and unit
+//           (d, k2), the lanes still missing (k2, w) OR the frontier lanes of
+//           w's in-neighbours in direction d until none is missing.
 //   commit  M_{j+1}[w] = NX[w], P[w] |= NX[w], NX[w] = 0 for every touched w;
 //           the touched list becomes the next frontier list.
 // The answer of lane i is {v : P[v][k] has bit i for a final slot k of i}.
@@ -39,7 +43,6 @@ namespace {
 
 constexpr int kLThreads = 256;
 constexpr int kLWarps = kLThreads / 32;
-constexpr int kLaneHub = 128;     // edges of one (vertex, direction) handled inline
 constexpr int kLaneChunk = 128;   // edges per chunk of a longer row (one warp, 4 rounds)
 constexpr uint64_t kLaneBarrierNs = 4000000000ull;
 
@@ -175,7 +178,7 @@ __device__ void lane_expand_vertices(const LParams &p, int j, uint64_t *sm_M, ui
             if (!lane_aggregate(p, dir, sm_M, sm_X)) continue;
             int32_t b, e;
             adj_row(p.adj[dir.d], v, b, e);
-            const int32_t e1 = min(e, b + kLaneHub);
+            const int32_t e1 = min(e, b + p.lane_hub);
             if (e > e1 && lane == 0) {
                 const unsigned long long nch =
                     (unsigned long long)((e - e1 + kLaneChunk - 1) / kLaneChunk);
@@ -225,6 +228,88 @@ __device__ void lane_expand_hubs(const LParams &p, int j, uint64_t *sm_M, uint64
         __syncwarp();
     }
     (void)lane;
+}
+
+// Pull level j (a warp per vertex w, grid-stride over all vertices): for each
+// unit (d, k2), need = lanes that reached new pairs at level j, whose
+// automaton can enter k2 by d, and that have not visited (k2, w); the warp
+// ORs X_{d,k2}[u] = OR_s M[u][k_s] & mask_s over the in-neighbours u of w
+// (rows of the inverse direction), 32 at a time, and stops when the OR
+// covers need.  New lanes go to NX[w][k2]; w joins the touched list once.
+__device__ void lane_pull(const LParams &p, int j) {
+    const int cur = j % 3, nxt = (j + 1) % 3;
+    const uint64_t *M = (j & 1) ? p.M1 : p.M0;
+    int32_t *TV = lane_list(p, nxt);
+    unsigned long long *tvc = &p.c->list_count[nxt];
+    const unsigned lane = lane_id();
+    uint64_t live[kLW];
+#pragma unroll
+    for (int lw = 0; lw < kLW; lw++)
+        live[lw] = *(volatile unsigned long long *)&p.c->lane_new[cur][lw] & p.dyn->active[lw];
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int n_dirs = p.dyn->n_dirs;
+    for (long long w = gw; w < p.n; w += nw) {
+        bool first = false;
+        for (int D = 0; D < n_dirs; D++) {
+            const LDir dir = p.dirs[D];
+            const int dinv = dir.d < p.adj_half ? dir.d + p.adj_half : dir.d - p.adj_half;
+            int32_t b, e;
+            adj_row(p.adj[dinv], (int32_t)w, b, e);
+            if (b >= e) continue;  // warp-uniform
+            for (int uu = 0; uu < dir.unit_count; uu++) {
+                const LUnit U = p.units[dir.unit_first + uu];
+                const size_t row = ((size_t)w * p.K + U.k2) * kLW;
+                uint64_t need[kLW];
+                bool any = false;
+#pragma unroll
+                for (int lw = 0; lw < kLW; lw++) {
+                    uint64_t reach = 0;
+                    for (int sI = 0; sI < U.src_count; sI++) reach |= p.srcs[U.src_first + sI].mask[lw];
+                    need[lw] = live[lw] & reach & ~__ldcg(p.P + row + lw);
+                    any = any || need[lw];
+                }
+                if (!any) continue;  // warp-uniform (every lane computed the same)
+                uint64_t acc[kLW] = {0, 0, 0, 0};
+                for (int32_t base = b; base < e; base += 32) {
+                    const int32_t k = base + (int32_t)lane;
+                    uint64_t x[kLW] = {0, 0, 0, 0};
+                    if (k < e) {
+                        const int32_t u = __ldg(p.adj[dinv].nbr + k);
+                        for (int sI = 0; sI < U.src_count; sI++) {
+                            const LSrc &S = p.srcs[U.src_first + sI];
+                            const size_t mr = ((size_t)u * p.K + S.k) * kLW;
+#pragma unroll
+                            for (int lw = 0; lw < kLW; lw++) x[lw] |= __ldcg(M + mr + lw) & S.mask[lw];
+                        }
+                    }
+                    bool done = true;
+#pragma unroll
+                    for (int lw = 0; lw < kLW; lw++) {
+                        const uint32_t lo = __reduce_or_sync(kFull, (uint32_t)(x[lw] & need[lw]));
+                        const uint32_t hi = __reduce_or_sync(kFull, (uint32_t)((x[lw] & need[lw]) >> 32));
+                        acc[lw] |= ((uint64_t)hi << 32) | lo;
+                        done = done && (acc[lw] == need[lw]);
+                    }
+                    if (done) break;  // warp-uniform
+                }
+                if ((int)lane < kLW && acc[lane]) {
+                    const unsigned long long old =
+                        atomicOr((unsigned long long *)(p.NX + row + lane), (unsigned long long)acc[lane]);
+                    if (old == 0ull) first = true;
+                }
+            }
+        }
+        // w joins the touched list once (its touched bit decides)
+        bool app = false;
+        const bool fw = __any_sync(kFull, first);
+        if (fw && lane == 0) {
+            const unsigned long long bit = 1ull << (w & 63);
+            const unsigned long long old = atomicOr((unsigned long long *)(p.tv + (w >> 6)), bit);
+            app = !(old & bit);
+        }
+        warp_append_i32(app, (int32_t)w, TV, tvc);
+    }
 }
 
 // Commit of level j -> j+1 (grid-stride, a warp per list entry).
@@ -288,10 +373,16 @@ __global__ void __launch_bounds__(kLThreads) lane_batch_kernel(LParams p, int32_
     uint64_t *sm_M = lsm + (size_t)warp * 2 * p.K * kLW;
     uint64_t *sm_X = sm_M + p.K * kLW;
     for (int j = 0;; j++) {
-        lane_expand_vertices(p, j, sm_M, sm_X);
-        if (!lane_barrier(p.c)) return;
-        lane_expand_hubs(p, j, sm_M, sm_X);
-        if (!lane_barrier(p.c)) return;
+        const unsigned long long nA = *(volatile unsigned long long *)&p.c->list_count[j % 3];
+        if (p.pull_div > 0 && nA * (unsigned long long)p.pull_div > (unsigned long long)p.n) {
+            lane_pull(p, j);
+            if (!lane_barrier(p.c)) return;
+        } else {
+            lane_expand_vertices(p, j, sm_M, sm_X);
+            if (!lane_barrier(p.c)) return;
+            lane_expand_hubs(p, j, sm_M, sm_X);
+            if (!lane_barrier(p.c)) return;
+        }
         lane_commit(p, j);
         if (!lane_barrier(p.c)) return;
         const unsigned long long nT =
@@ -487,6 +578,8 @@ __global__ void lane_seed_step_kernel(LParams p, const int32_t *__restrict__ see
         const size_t idx = ((size_t)s[0] * p.K + s[1]) * kLW + s[2];
         atomicOr((unsigned long long *)(M + idx), (unsigned long long)m);
         atomicOr((unsigned long long *)(p.P + idx), (unsigned long long)m);
+        // the seeded lanes have a frontier at this level (a pull reads it)
+        atomicOr(&p.c->lane_new[step % 3][s[2]], (unsigned long long)m);
     }
     int32_t *A = lane_list(p, step % 3);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_verts; i += gridDim.x * blockDim.x) {
@@ -583,7 +676,7 @@ rpq_status lane_ws_alloc(LaneWorkspace *ws, const rpq_graph *g, int K) {
     const size_t list_cap = (size_t)g->n + 2 * kLanes;  // distinct vertices + seeds of one step
     long long hub_cap = 1024, chunk_cap = 1024;
     for (int d = 0; d < 2 * g->L; d++) {
-        hub_cap += g->adj[d].nnz / kLaneHub + 1;
+        hub_cap += g->adj[d].nnz / kLaneHubMin + 1;
         chunk_cap += g->adj[d].nnz / kLaneChunk + 1;
     }
     ws->n = g->n;
@@ -675,6 +768,12 @@ LParams lane_params(rpq_graph *g, LaneWorkspace *ws, size_t o_dyn, size_t o_dirs
     p.hub_cap = ws->hub_cap;
     p.chunk_cap = ws->chunk_cap;
     p.c = ws->ctr.as<LaneCounters>();
+    p.adj_half = g->L;
+    // the graph's tuning; RPQ_LANE_HUB and RPQ_LANE_PULL_DIV override
+    const char *h = getenv("RPQ_LANE_HUB");
+    const char *pd = getenv("RPQ_LANE_PULL_DIV");
+    p.lane_hub = std::max(kLaneHubMin, h ? atoi(h) : g->lane_hub);
+    p.pull_div = std::max(0, pd ? atoi(pd) : g->lane_pull_div);
     return p;
 }
 
@@ -1150,4 +1249,71 @@ extern "C" rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_n
         return fail(RPQ_ERR_CAPACITY, "batch answers hold %lld vertices, capacity %lld",
                     (long long)total, (long long)capacity);
     return RPQ_OK;
+}
+
+// ------------------------------------------------------ batch autotune --
+namespace rpq {
+namespace {
+// Lane engine tuning: times the sample batch (lane groups of up to 256) on
+// the lane kernel under every (inline row length, pull divisor) pair and
+// keeps the fastest by device time.
+rpq_status autotune_batch(rpq_graph *g, int n, const rpq_nfa *const *nfas, const int32_t *sources,
+                          int32_t *hub_out, int32_t *pull_out, cudaStream_t st) {
+    static const int32_t kHubs[] = {32, 64, 128, 256};
+    static const int32_t kPulls[] = {0, 2, 4, 8, 16};
+    std::vector<const Automaton *> autos(n);
+    for (int i = 0; i < n; i++) autos[i] = &nfas[i]->a;
+    const int32_t keep_h = g->lane_hub, keep_p = g->lane_pull_div;
+    double best = -1;
+    int32_t best_h = keep_h, best_p = keep_p;
+    std::vector<int64_t> offs((size_t)kLanes + 1);
+    std::vector<int32_t> lv(kLanes);
+    for (int32_t h : kHubs) {
+        for (int32_t pd : kPulls) {
+            g->lane_hub = h;
+            g->lane_pull_div = pd;
+            double total = 0;
+            for (int rep = 0; rep < 2; rep++) {  // the first pass warms the workspace
+                total = 0;
+                for (int g0 = 0; g0 < n; g0 += kLanes) {
+                    const int cnt = std::min(kLanes, n - g0);
+                    float ms = 0;
+                    rpq_status s = lane_run_group(g, autos.data() + g0, sources + g0, cnt, 0,
+                                                  nullptr, false, 0, offs.data(), lv.data(), &ms, st);
+                    if (s != RPQ_OK) {
+                        g->lane_hub = keep_h;
+                        g->lane_pull_div = keep_p;
+                        return s;
+                    }
+                    total += ms;
+                }
+            }
+            if (best < 0 || total < best) {
+                best = total;
+                best_h = h;
+                best_p = pd;
+            }
+        }
+    }
+    g->lane_hub = best_h;
+    g->lane_pull_div = best_p;
+    if (hub_out) *hub_out = best_h;
+    if (pull_out) *pull_out = best_p;
+    return RPQ_OK;
+}
+}  // namespace
+}  // namespace rpq
+
+extern "C" rpq_status rpq_graph_autotune_batch(rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
+                                               const int32_t *sources, int32_t *lane_hub_out,
+                                               int32_t *pull_div_out, void *stream) {
+    clear_error();
+    if (!g || n <= 0 || !nfas || !sources) return fail(RPQ_ERR_INVALID, "bad argument");
+    for (int32_t i = 0; i < n; i++) {
+        if (!nfas[i]) return fail(RPQ_ERR_INVALID, "automaton %d is null", i);
+        if (sources[i] < 0 || sources[i] >= g->n)
+            return fail(RPQ_ERR_INVALID, "source %d outside [0, %d)", sources[i], g->n);
+    }
+    return autotune_batch(g, n, nfas, sources, lane_hub_out, pull_div_out,
+                          static_cast<cudaStream_t>(stream));
 }

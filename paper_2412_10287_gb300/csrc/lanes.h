@@ -73,7 +73,15 @@ struct LParams {
     int32_t *hub_cmap;           // chunk -> hub entry
     long long hub_cap, chunk_cap;
     LaneCounters *c;
+    // tuning (rpq_graph_autotune_batch): edges of a (vertex, direction) row
+    // pushed inline before the rest goes to chunks (>= kLaneHubMin); pull
+    // instead of push when the frontier holds more than n / pull_div
+    // vertices (0: never pull)
+    int32_t lane_hub, pull_div;
+    int32_t adj_half;  // L: direction d and d +- L are inverse to each other
 };
+
+constexpr int kLaneHubMin = 32;  // smallest inline row length (sizes the hub lists)
 
 // Device workspace of one lane group (sized for n vertices and K slots).
 struct LaneWorkspace : WorkspaceBase {

@@ -195,6 +195,10 @@ struct KParams {
     // push levels with more edge mass than this read the visited word before
     // each atomicOr (most of their targets are already visited)
     long long precheck_mass;
+    // states [0, dense_clear) entered the launch with visited bits that no
+    // list holds (pairs excluded beforehand): their rows of P are cleared
+    // densely at the end, and the one-CTA answer path is not taken
+    int32_t dense_clear;
     Counters *c;
     // output
     int32_t *out_list;
@@ -1843,7 +1847,7 @@ __device__ void clear_state(const KParams &p, const Shared &sh, bool finals_too,
         const long long vend = sh.vstart[q] + (long long)sh.fl[q];
         const int32_t *lst = p.VL + (size_t)q * p.n;
         uint64_t *Pq = p.P + (size_t)q * W;
-        if (vend * 8 < W) {
+        if (vend * 8 < W && q >= p.dense_clear) {
             for (long long i0 = first; i0 < vend; i0 += 4 * stride) {
                 int32_t v[4];
 #pragma unroll
@@ -1869,7 +1873,7 @@ constexpr long long kSoloClear = 4096;  // visited pairs CTA 0 clears through th
 // kSoloAnswer entries (before removing duplicates across final states) and
 // at most kSoloClear visited pairs.  Same result on every CTA.
 __device__ bool solo_finish(const KParams &p, const Shared &sh) {
-    if (p.out_bits) return false;
+    if (p.out_bits || p.dense_clear > 0) return false;
     long long t = 0, v = 0;
     for (int q = 0; q < p.S; q++) {
         const long long e = sh.vstart[q] + (long long)sh.fl[q];
@@ -2296,6 +2300,30 @@ __global__ void reset_levels_kernel(int32_t *pair_level, const int32_t *VL, int3
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
              i += (long long)gridDim.x * blockDim.x)
             pair_level[(size_t)q * n + __ldg(lst + i)] = -1;
+    }
+}
+
+// Before a pruned launch: rows q < S0 of P become the complement of
+// `allowed` (those pairs count as visited, so the traversal never enters
+// them).  Bits past vertex n - 1 are set too; nothing reads them.
+__global__ void premask_kernel(uint64_t *P, const uint64_t *allowed, int64_t words) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        P[i] = ~__ldg(allowed + i);
+}
+
+// After a query with pair levels: bit v of row q is set iff (q, v) was
+// visited (one thread per output word).
+__global__ void reach_bits_kernel(const int32_t *pair_level, int32_t n, int32_t S, int64_t W,
+                                  uint64_t *out) {
+    const int64_t words = (int64_t)S * W;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = i / W, w0 = (i - q * W) * 64;
+        uint64_t b = 0;
+        for (int k = 0; k < 64 && w0 + k < n; k++)
+            if (__ldg(pair_level + q * n + w0 + k) >= 0) b |= 1ull << k;
+        out[i] = b;
     }
 }
 
@@ -2811,6 +2839,14 @@ rpq_status path_outputs(const rpq_graph *g, const Automaton &a, QueryWorkspace *
                                              cudaMemcpyDeviceToHost, st));
         }
     }
+    if (x->reach_bits_out) {
+        const int64_t W = ((int64_t)g->n + 63) / 64;
+        const int blocks = (int)std::min<int64_t>((int64_t)dev_sms * 8, ((int64_t)a.S * W + 255) / 256);
+        reach_bits_kernel<<<blocks, 256, 0, st>>>(ws->plevel.as<int32_t>(), g->n, a.S, W,
+                                                   x->reach_bits_out);
+        RPQ_CUDA_TRY(cudaGetLastError());
+        note_launch();
+    }
     {
         const int blocks = dev_sms * 4;
         reset_levels_kernel<<<blocks, 256, 0, st>>>(ws->plevel.as<int32_t>(), ws->VL.as<int32_t>(),
@@ -2863,7 +2899,7 @@ rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_
     const bool want_host = !out_list_dev && (host_list || out_host_list);
     tl_answer.valid = false;  // a host answer lives until this thread's next query
     const bool multi = x && x->sources;
-    const bool levels = x && (x->out_levels_dev || x->witness);
+    const bool levels = x && (x->out_levels_dev || x->witness || x->reach_bits_out);
     if (multi) {
         if (x->n_sources <= 0) return fail(RPQ_ERR_INVALID, "empty source set");
         for (int32_t i = 0; i < x->n_sources; i++)
@@ -2939,6 +2975,24 @@ rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_
     p.sort_cnt = ws->sortc.as<uint32_t>();
     p.epoch = ++ws->epoch;
     p.clear_first = ws->dirty ? 1 : 0;
+    if (x && x->premask_bits) {
+        // the kernel must not clear P after the rows are pre-set: a dirty
+        // workspace is cleared here first
+        const size_t bits_bytes = sizeof(uint64_t) * (size_t)a.S * ws->W;
+        if (ws->dirty) {
+            RPQ_CUDA_TRY(cudaMemsetAsync(ws->P.p, 0, bits_bytes, st));
+            for (int k = 0; k < 3; k++) RPQ_CUDA_TRY(cudaMemsetAsync(ws->F[k].p, 0, bits_bytes, st));
+            p.clear_first = 0;
+        }
+        const int64_t words = (int64_t)x->premask_states * ws->W;
+        int sms = 0;
+        RPQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+        premask_kernel<<<(int)std::min<int64_t>((int64_t)sms * 8, (words + 255) / 256), 256, 0, st>>>(
+            ws->P.as<uint64_t>(), x->premask_bits, words);
+        RPQ_CUDA_TRY(cudaGetLastError());
+        note_launch();
+        p.dense_clear = x->premask_states;
+    }
     QueryResult *hr = reinterpret_cast<QueryResult *>(hs + kResultOffset);
     p.result = ws->result_dev;
     p.P = ws->P.as<uint64_t>();

@@ -111,11 +111,29 @@ struct QueryExtras {
     int32_t *path_v = nullptr, *path_s = nullptr;
     int32_t path_cap = 0;
     int32_t path_len = -1;
+    // device [S][ceil(n/64)] words: after the query, bit v of row q is set
+    // iff the pair (q, v) was visited
+    uint64_t *reach_bits_out = nullptr;
+    // device [premask_states][ceil(n/64)] words: before the query, the pairs
+    // (q, v), q < premask_states, whose bit is clear are marked visited, so
+    // the traversal never enters them (pruning); their P rows are cleared
+    // densely at the end
+    const uint64_t *premask_bits = nullptr;
+    int32_t premask_states = 0;
 };
 rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_t source,
                         int32_t max_levels, int32_t *out_list_dev, int64_t capacity,
                         uint64_t *out_bits_dev, int32_t *out_host_list, rpq_stats *stats,
                         int64_t *count, void *stream, int grid_div, bool host_list = false);
+// Rare label first (rare.cu): when every accepted word of `a` reads a label
+// direction with few edges, the query runs as a backward search from that
+// label's edges and a forward search pruned to what it found; *applied
+// tells whether it did (else nothing ran and the caller runs the plain
+// query).  Same output contract as run_query.
+rpq_status run_query_rare(rpq_graph *g, const Automaton &a, int32_t source, int32_t max_levels,
+                          int32_t *out_list_dev, int64_t capacity, int32_t *out_host_list,
+                          rpq_stats *stats, int64_t *count, void *stream, bool host_list,
+                          bool *applied);
 // The calling thread's last host answer (run_query with a host list).
 rpq_status last_host_answer(const int32_t **answer, int64_t *count);
 

@@ -99,6 +99,10 @@ struct rpq_server {
     // failure (back-off) and raised again as queries complete
     int slot_cap = 0;
     int64_t oom_retries = 0;
+    // engine 0: grid share divisor of a query that finds the queue empty (2:
+    // at 2,000 q/s on rmat20 half the grid gave p50 0.17 ms and p99 1.2 ms,
+    // the whole grid 0.39 / 1.3 ms, a quarter 0.08 / 1.7 ms)
+    int idle_div = 2;
     // statistics
     int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, level_steps = 0;
     std::vector<double> latency_ms;
@@ -391,9 +395,12 @@ void worker_main(rpq_server *s) {
 // query is admitted when a worker is free and its workspace fits the memory
 // budget beside those of the queries in flight (in arrival order: a query
 // that does not fit waits, and so do the ones behind it).  Its share of the
-// persistent grid follows the load: a query that runs alone, with nothing
-// queued, takes the whole grid; otherwise 1/slots of it, so that up to
-// `slots` queries overlap on the device.
+// persistent grid follows the queue at admission: 1/k of the grid when it
+// and k - 1 queued queries are waiting (at most 1/slots), so a burst
+// overlaps on the device, while a query that finds the queue empty takes
+// half the grid (RPQ_SERVE_IDLE_DIV), so that one arriving meanwhile finds
+// room beside it.  (A query admitted while others fill the grid waits for
+// room either way: a cooperative launch starts only when all its CTAs fit.)
 void slot_worker_main(rpq_server *s) {
     cudaSetDevice(s->g->device);
     cudaStream_t st = nullptr;
@@ -419,7 +426,7 @@ void slot_worker_main(rpq_server *s) {
             s->queue.pop_front();
             need = query_bytes(s, q.a);
             admit_account(s, need);
-            if (s->inflight_n == 1 && s->queue.empty()) grid_div = 1;
+            grid_div = std::min(s->lanes_max, std::max(s->idle_div, 1 + (int)s->queue.size()));
         }
         int64_t cnt = 0;
         rpq_stats qs{};
@@ -482,6 +489,8 @@ extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_confi
         s->queue_cap = c.queue_capacity > 0 ? (size_t)c.queue_capacity : 65536;
         s->budget = c.memory_budget;
         s->slot_cap = slots;
+        const char *idv = getenv("RPQ_SERVE_IDLE_DIV");
+        s->idle_div = std::max(1, std::min(slots, idv ? atoi(idv) : 2));
         rpq_server *raw = s.get();
         for (int k = 0; k < slots; k++) s->slot_workers.emplace_back(slot_worker_main, raw);
         *out = s.release();

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "RPQ_OK", 1: "RPQ_ERR_INVALID", 2: "RPQ_ERR_PARSE", 3: "RPQ_E
 # Every symbol include/rpq.h declares.
 EXPORTED = (
     "rpq_set_allocator", "rpq_graph_load", "rpq_graph_free", "rpq_graph_info", "rpq_graph_export",
-    "rpq_graph_autotune", "rpq_graph_set_hybrid",
+    "rpq_graph_autotune", "rpq_graph_autotune_batch", "rpq_graph_set_hybrid",
+    "rpq_graph_set_rare_plan",
     "rpq_nfa_compile", "rpq_nfa_from_transitions", "rpq_nfa_free", "rpq_nfa_info",
     "rpq_nfa_export", "rpq_nfa_accepts", "rpq_nfa_reverse", "rpq_query", "rpq_last_answer",
     "rpq_query_noalloc",
@@ -101,6 +102,8 @@ def lib():
             "rpq_graph_export": [p, i32, i32, p, p, i64],
             "rpq_graph_autotune": [p, i32, p, p, p, p, p, p],
             "rpq_graph_set_hybrid": [p, i64],
+            "rpq_graph_autotune_batch": [p, i32, p, p, p, p, p],
+            "rpq_graph_set_rare_plan": [p, i64],
             "rpq_nfa_compile": [ctypes.c_char_p, i32, pp],
             "rpq_nfa_from_transitions": [i32, i32, i32, p, p, p, i32, p, i32, p, pp],
             "rpq_nfa_info": [p, p, p, p],
@@ -265,10 +268,28 @@ def rpq_graph_export(g: Graph, label: int, inverse: bool):
     return off, nbr[: int(off[-1])]
 
 
+def rpq_graph_autotune_batch(g: Graph, nfas, sources, stream=None):
+    """Tunes the bit-lane engine (inline row length, pull divisor) on sample
+    queries; returns (lane_hub, pull_div)."""
+    n = len(nfas)
+    handles = (ctypes.c_void_p * n)(*[x.h.value for x in nfas])
+    src, psrc = _host_i32(sources)
+    h, pdv = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().rpq_graph_autotune_batch(g.h, n, handles, psrc, ctypes.byref(h), ctypes.byref(pdv),
+                                          _stream_handle(stream)))
+    return h.value, pdv.value
+
+
 def rpq_graph_set_hybrid(g: Graph, switch_pairs: int):
     """Algorithm 2 while fewer than ``switch_pairs`` pairs are visited, then
     Algorithm 1 (section 5.1's hybrid); 0 turns it off."""
     _check(lib().rpq_graph_set_hybrid(g.h, int(switch_pairs)))
+
+
+def rpq_graph_set_rare_plan(g: Graph, max_edges: int):
+    """Rare label first for single queries whose accepted words all read a
+    label direction with at most ``max_edges`` edges; 0 turns it off."""
+    _check(lib().rpq_graph_set_rare_plan(g.h, int(max_edges)))
 
 
 def rpq_graph_autotune(g: Graph, nfas, sources, stream=None):

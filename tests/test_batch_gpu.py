@@ -28,18 +28,16 @@ def load(g):
     return R.rpq_graph_load(g.n, g.n_labels, g.src, g.dst, g.lab)
 
 
-@pytest.fixture(params=["slots", "lanes"], autouse=True)
-def engine(request):
-    """Every batch test runs on both engines: concurrent query slots and bit lanes."""
-    import os
-
-    old = os.environ.get("RPQ_BATCH_ENGINE")
-    os.environ["RPQ_BATCH_ENGINE"] = request.param
+@pytest.fixture(params=["slots", "lanes", "lanes_pull"], autouse=True)
+def engine(request, monkeypatch):
+    """Every batch test runs on both engines: concurrent query slots and bit
+    lanes -- the latter also with every level pulling and the shortest
+    inline rows (the other ends of the lane engine's tuning range)."""
+    monkeypatch.setenv("RPQ_BATCH_ENGINE", "slots" if request.param == "slots" else "lanes")
+    if request.param == "lanes_pull":
+        monkeypatch.setenv("RPQ_LANE_PULL_DIV", "1000000000")
+        monkeypatch.setenv("RPQ_LANE_HUB", "32")
     yield request.param
-    if old is None:
-        os.environ.pop("RPQ_BATCH_ENGINE", None)
-    else:
-        os.environ["RPQ_BATCH_ENGINE"] = old
 
 
 def test_batch_shared_automaton_many_sources():
@@ -167,3 +165,21 @@ def test_fresh_workspaces_on_reused_memory(engine):
     for i in range(48):
         exp = og.ssr(oracle_compile(texts[i % len(texts)], 4), srcs[i])["answer"]
         assert got[i].tolist() == exp.tolist(), i
+
+
+def test_lane_autotune_keeps_answers(engine):
+    """The lane engine's autotuner picks an inline row length and a pull
+    divisor from its candidate sets; the answers do not change."""
+    if engine != "lanes":
+        pytest.skip("one run is enough")
+    g = W.rmat_graph(13, 1 << 17, 4, seed=47)
+    gg = load(g)
+    og = O.OracleGraph(g.n, 4, g.src, g.dst, g.lab)
+    srcs = W.below(48, 1, 64, g.n).tolist()
+    nfa = R.rpq_nfa_compile("(0|^1)*/2", 4)
+    hub, pdv = R.rpq_graph_autotune_batch(gg, [nfa] * 64, srcs)
+    assert hub in (32, 64, 128, 256) and pdv in (0, 2, 4, 8, 16)
+    got = R.rpq_query_batch(gg, [nfa] * 64, srcs)
+    on = oracle_compile("(0|^1)*/2", 4)
+    for i in range(64):
+        assert got[i].tolist() == og.ssr(on, srcs[i])["answer"].tolist(), i

@@ -158,3 +158,18 @@ def test_oracle_sample_is_bounded_and_counts_what_ran():
     assert 1 <= r["queries"] <= 2 and r["cores"] == 2 and r["kind"] == "oracle"
     r = bench.oracle_sample(w, 30.0, max_threads=2)
     assert r["queries"] == len(qs) and r["value"] == pytest.approx(r["queries"] / r["wall_s"])
+
+
+def test_rare_queries_end_in_a_rare_label():
+    import numpy as np
+
+    from paper_2412_10287_gb300 import workloads as W
+
+    g = W.chung_lu_graph(200_000, 2_000_000, 2.1, 500, 1.1, seed=2)
+    counts = np.bincount(g.lab, minlength=500)
+    qs = bench.rare_queries(g, 12)
+    assert len(qs) == 12
+    for q in qs:
+        last = int(q.regex.rsplit("/", 1)[1])
+        assert 0 < counts[last] <= bench.RARE_MAX
+        assert 0 <= q.source < g.n

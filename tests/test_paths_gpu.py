@@ -308,3 +308,71 @@ def test_hybrid_rmat_switches_to_algorithm_1(rmat14):
             assert R.rpq_query_multi(gg, nfa, srcs).tolist() == og.query(on, srcs)["answer"].tolist()
     finally:
         R.rpq_graph_set_hybrid(gg, 0)
+
+
+# ------------------------------------------------------- rare label first --
+# Section 5.4-5.5 / section 6: when every accepted word reads a rare label,
+# a backward search from that label's edges prunes the forward search.  The
+# answer is the query's answer whatever the plan.
+
+def test_rare_plan_tiny_random():
+    for seed in range(80):
+        g = W.tiny_graph(seed + 9600, max_n=12, max_m=30)
+        S, trans, starts, finals = W.tiny_automaton(seed + 9700, g.n_labels, max_states=5,
+                                                    max_trans=10)
+        og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+        gg = load(g)
+        R.rpq_graph_set_rare_plan(gg, 1 << 40)  # every label counts as rare
+        dn = R.rpq_nfa_from_transitions(S, g.n_labels, trans, starts, finals)
+        on = Nfa(S, g.n_labels, trans, starts, finals)
+        for src in range(0, g.n, max(1, g.n // 4)):
+            for k in (0, 2):
+                exp = og.ssr(on, src, k)["answer"].tolist()
+                assert R.rpq_query(gg, dn, src, k).tolist() == exp, (seed, src, k, trans)
+        og.close()
+
+
+def test_rare_plan_knowledge_base_graph():
+    """a/b*/c and a/(b|^c)*/d with a rare last label on a power-law graph of
+    500 labels: the same answers as the plain search and the oracle (there
+    the rare labels' edges sit in the giant component, so the backward
+    search prunes little)."""
+    g = W.chung_lu_graph(1_000_000, 10_000_000, 2.1, 500, 1.1, seed=2)
+    gg = load(g)
+    og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+    counts = np.bincount(g.lab, minlength=500)
+    rare = [int(x) for x in np.flatnonzero((counts > 0) & (counts < 2000))[:6]]
+    srcs = W.below(97, 1, 6, g.n).tolist()
+    fewer = 0
+    for i, c in enumerate(rare):
+        for text in (f"0/1*/{c}", f"1/(0|^2)*/{c}", f"(0|1)*/{c}/3"):
+            s = srcs[i]
+            R.rpq_graph_set_rare_plan(gg, 0)
+            plain, st0 = R.rpq_query(gg, R.rpq_nfa_compile(text, 500), s, with_stats=True)
+            R.rpq_graph_set_rare_plan(gg, 10000)
+            ruled, st1 = R.rpq_query(gg, R.rpq_nfa_compile(text, 500), s, with_stats=True)
+            assert ruled.tolist() == plain.tolist(), (text, s)
+            assert ruled.tolist() == og.ssr(oracle_compile(text, 500), s)["answer"].tolist()
+    og.close()
+
+
+def test_rare_plan_prunes_a_long_path():
+    """0/1*/2 from the head of a 5,000-vertex path of label 1 whose only
+    label-2 edge leaves vertex 10: the plain search walks the whole path
+    (5,000 levels); rare label first walks back from the one label-2 edge,
+    keeps the first 11 path vertices and answers in a dozen levels."""
+    m = 5000
+    src = np.concatenate([[0], np.arange(1, m, dtype=np.int32), [11]]).astype(np.int32)
+    dst = np.concatenate([[1], np.arange(2, m + 1, dtype=np.int32), [m + 1]]).astype(np.int32)
+    lab = np.concatenate([[0], np.ones(m - 1, np.int32), [2]]).astype(np.int32)
+    g = W.Graph("path", m + 2, 3, src, dst, lab)
+    gg = load(g)
+    nfa = R.rpq_nfa_compile("0/1*/2", 3)
+    plain, st0 = R.rpq_query(gg, nfa, 0, with_stats=True)
+    R.rpq_graph_set_rare_plan(gg, 10)
+    ruled, st1 = R.rpq_query(gg, nfa, 0, with_stats=True)
+    assert plain.tolist() == ruled.tolist() == [m + 1]
+    exp = O.ssr(g.n, 3, src, dst, lab, oracle_compile("0/1*/2", 3), 0)["answer"].tolist()
+    assert ruled.tolist() == exp
+    assert st0["levels"] >= m - 1 and st1["levels"] <= 13
+    assert st1["visited_pairs"] < 30 < st0["visited_pairs"]
