@@ -346,8 +346,12 @@ rpq_status rpq_query_witness(const rpq_graph *g, const rpq_nfa *nfa, int32_t n_s
  * concatenated: query i's vertices (ascending) are
  * out_vertices[out_offsets[i] .. out_offsets[i+1]).  out_offsets (n+1 int64)
  * is always filled; RPQ_ERR_CAPACITY when the total exceeds `capacity`.
- * `stats` may be NULL or an array of n entries.  Automata may have up to 64
- * states each. */
+ * `stats` may be NULL or an array of n entries: on the slots engine each
+ * query's own counters; on the bit lanes the level count, the answer size,
+ * the group's kernel time, and in product_edges the edges the group's
+ * shared pass read for all of its queries together (the same value for
+ * every query of a group of up to 256; the other counters are -1).
+ * Automata may have up to 64 states each. */
 rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_nfa *const *nfas,
                            const int32_t *sources, int32_t max_levels, int64_t *out_offsets,
                            int32_t *out_vertices, int64_t capacity, rpq_stats *stats,

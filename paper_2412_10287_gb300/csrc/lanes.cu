@@ -271,7 +271,9 @@ __device__ void lane_pull(const LParams &p, int j) {
                 }
                 if (!any) continue;  // warp-uniform (every lane computed the same)
                 uint64_t acc[kLW] = {0, 0, 0, 0};
+                int32_t scanned = 0;
                 for (int32_t base = b; base < e; base += 32) {
+                    scanned = min(e, base + 32) - b;
                     const int32_t k = base + (int32_t)lane;
                     uint64_t x[kLW] = {0, 0, 0, 0};
                     if (k < e) {
@@ -293,6 +295,7 @@ __device__ void lane_pull(const LParams &p, int j) {
                     }
                     if (done) break;  // warp-uniform
                 }
+                if (lane == 0) atomicAdd(&p.c->edges, (unsigned long long)scanned);
                 if ((int)lane < kLW && acc[lane]) {
                     const unsigned long long old =
                         atomicOr((unsigned long long *)(p.NX + row + lane), (unsigned long long)acc[lane]);
@@ -911,7 +914,7 @@ rpq_status lane_harvest(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
 rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int32_t *sources,
                           int count, int32_t max_levels, int32_t *out, bool out_is_dev,
                           int64_t capacity, int64_t *offsets, int32_t *lane_levels, float *ms,
-                          cudaStream_t st) {
+                          cudaStream_t st, int64_t *edges_out = nullptr) {
     int K = 1;
     for (int i = 0; i < count; i++) K = std::max(K, autos[i]->S);
     if (K > kLaneMaxSlots) return fail(RPQ_ERR_INVALID, "automaton with more than 64 states");
@@ -1051,6 +1054,7 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     for (int i = 0; i <= count; i++) offsets[i] = offs[i];
     for (int i = 0; i < count; i++) lane_levels[i] = hl[i];
     if (ms) *ms = kms;
+    if (edges_out) *edges_out = (int64_t)hc.edges;
     const int64_t total = offs[count];
     if (!out_is_dev && total <= capacity && total > 0) memcpy(out, host_ans.data(), 4 * total);
     lane_ws_release(g, std::move(ws));
@@ -1220,10 +1224,11 @@ extern "C" rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_n
         std::vector<int64_t> offs(cnt + 1);
         std::vector<int32_t> lv(cnt);
         float ms = 0;
+        int64_t lane_edges = 0;
         const int64_t room = overflow ? 0 : std::max<int64_t>(0, capacity - total);
         rpq_status s = lane_run_group(gm, autos.data() + g0, sources + g0, cnt, max_levels,
                                       out_vertices ? out_vertices + total : nullptr, dev, room,
-                                      offs.data(), lv.data(), &ms, st);
+                                      offs.data(), lv.data(), &ms, st, &lane_edges);
         if (s != RPQ_OK) return s;
         for (int i = 0; i < cnt; i++) out_offsets[g0 + i + 1] = total + offs[i + 1];
         if (stats) {
@@ -1232,7 +1237,8 @@ extern "C" rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_n
                 x.levels = lv[i];
                 x.visited_pairs = -1;
                 x.expanded_pairs = -1;
-                x.product_edges = -1;
+                // the group's shared pass: the same count for every query of it
+                x.product_edges = lane_edges;
                 x.push_bytes = -1;
                 x.answer_count = offs[i + 1] - offs[i];
                 x.push_unit_levels = -1;

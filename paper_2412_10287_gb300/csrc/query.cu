@@ -2578,6 +2578,18 @@ std::unique_ptr<QueryWorkspace> ws_acquire(rpq_graph *g, int S, long long row_ne
     while (cc < chunk_need) cc *= 2;
     while (sc < srow_need) sc *= 2;
     *st = ws_alloc(w.get(), g, S_cap, rc, cc, sc, stream);
+    if (*st == RPQ_ERR_OOM) {
+        // memory is short: the graph's idle cached workspaces (of other
+        // shapes) go back to the allocator, then one more try
+        std::vector<std::unique_ptr<WorkspaceBase>> idle;
+        {
+            std::lock_guard<std::mutex> lk(g->ws_mu);
+            idle.swap(g->ws_free);
+        }
+        idle.clear();
+        w.reset(new QueryWorkspace());
+        *st = ws_alloc(w.get(), g, S_cap, rc, cc, sc, stream);
+    }
     if (*st != RPQ_OK) return nullptr;
     return w;
 }
