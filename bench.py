@@ -304,6 +304,10 @@ def workload_config(w, n_queries, extra=None):
          "n_vertices": w.graph.n, "n_edge_samples": w.graph.m, "n_labels": w.graph.n_labels,
          "queries_per_step": n_queries,
          "l2": "flushed between steps (256 MiB write)",
+         "timing": ("value, ms_per_step and latencies from the timed steps, queries without "
+                    "per-query statistics; roofline, product edges and bytes from as many "
+                    "further steps of the same queries with the library's statistics (CUDA "
+                    "events around every launch)"),
          "parallelism": "replicas (query-sharded, no collective)"}
     if extra:
         c.update(extra)
@@ -646,60 +650,80 @@ def run_serve(args, R, torch, g=None, gg=None):
 def measure_single(R, torch, w, gg, nfas, srcs, steps, warmup, stream, clock_dev=None,
                    dist=None):
     """Times `steps` steps of the workload's queries run one at a time with
-    device outputs (CUDA events around each step on the launching stream, L2
-    flushed in between).  Returns the per-step times, the per-query records
-    (host latency, stats, states), the launches counted and the clocks."""
+    device outputs and no per-query statistics (CUDA events around each step
+    on the launching stream, L2 flushed in between; the host latency of
+    every call), then `steps` more steps of the same queries with the
+    library's statistics, whose CUDA events around every launch give the
+    kernel's device time and whose counters give the algorithmic bytes.
+    Returns the step times and latencies of the first, the statistics
+    records of the second, the launches counted in the first and the clocks
+    over both."""
     out = torch.empty(w.graph.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    lean = R.QueryRunner(gg, out, stream)
+    full = R.QueryRunner(gg, out, stream, with_stats=True)
+    states = [nfa.info()[0] for nfa in nfas]
+    pc = time.perf_counter
 
-    def one_step(collect):
-        res = []
+    def lean_step(lat):
+        run = lean.run
         for nfa, s in zip(nfas, srcs):
-            t0 = time.perf_counter()
-            cnt, st = R.rpq_query(gg, nfa, s, out=out, stream=stream, with_stats=True)
-            if collect:
-                res.append((time.perf_counter() - t0, st, nfa.info()[0]))
-        return res
+            t0 = pc()
+            run(nfa, s)
+            lat.append(pc() - t0)
+
+    def stats_step(recs):
+        run, st = full.run, full.stats
+        for nfa, s, S in zip(nfas, srcs, states):
+            run(nfa, s)
+            recs.append((st.as_dict(), S))
+
+    def timed(body, sink):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k0 = R.rpq_kernel_launches()
+        e0.record(stream)
+        body(sink)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), R.rpq_kernel_launches() - k0
 
     for _ in range(warmup):
-        one_step(False)
+        lean_step([])
+        stats_step([])
     torch.cuda.synchronize()
-    step_ms, recs, k_timed = [], [], 0
+    step_ms, lat, recs, k_timed = [], [], [], 0
     clk = ClockSampler(clock_dev) if clock_dev is not None else None
     if clk:
         clk.__enter__()
     try:
         for _ in range(steps):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            if dist is not None:
-                dist.barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            k0 = R.rpq_kernel_launches()
-            e0.record(stream)
-            recs.extend(one_step(True))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            k_timed += R.rpq_kernel_launches() - k0
-            step_ms.append(e0.elapsed_time(e1))
+            ms, k = timed(lean_step, lat)
+            step_ms.append(ms)
+            k_timed += k
+        for _ in range(steps):
+            timed(stats_step, recs)
     finally:
         if clk:
             clk.__exit__(None, None, None)
-    return {"step_ms": step_ms, "recs": recs, "launches": k_timed,
+    return {"step_ms": step_ms, "lat": lat, "recs": recs, "launches": k_timed,
             "clocks": clk.summary() if clk else None}
 
 
-def latency_summary(recs):
-    lat = sorted(r[0] * 1000.0 for r in recs)
+def latency_summary(lat_s):
+    lat = sorted(x * 1000.0 for x in lat_s)
     return lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
 
 
 def algorithmic_bytes(recs, W_words):
     """Push-model bytes and the dense formulation's bitset sweeps (3 x S x W
     x 8 bytes per expanded level) of the recorded queries."""
-    push = sum(r[1]["push_bytes"] for r in recs)
-    sweep = sum(3 * r[2] * W_words * 8 * (r[1]["levels"] + 1) for r in recs)
+    push = sum(r[0]["push_bytes"] for r in recs)
+    sweep = sum(3 * r[1] * W_words * 8 * (r[0]["levels"] + 1) for r in recs)
     return push, sweep
 
 
@@ -715,16 +739,16 @@ def run_rmat20_extra(args, R, torch, g, gg):
     m = measure_single(R, torch, W.Workload("rmat20", g, qs), gg, nfas, srcs, args.steps,
                        args.warmup, stream)
     total_s = sum(m["step_ms"]) / 1000.0
-    p50, p99 = latency_summary(m["recs"])
+    p50, p99 = latency_summary(m["lat"])
     push, sweep = algorithmic_bytes(m["recs"], (g.n + 63) // 64)
-    launch_s = sum(r[1]["device_ms"] for r in m["recs"]) / len(m["recs"]) / 1000.0
+    launch_s = sum(r[0]["device_ms"] for r in m["recs"]) / len(m["recs"]) / 1000.0
     peak, _ = measured_peak()
     ach = (push + sweep) / len(m["recs"]) / launch_s / 1e9
     return {"workload": "rmat20: R-MAT scale 20, 8 labels Zipf(1.0), seed 1; 400 single-source "
                         "queries (a*, a.b*, (a|b)*.c, a^-.b*), one at a time",
             "queries_per_s": len(qs) * args.steps / total_s, "p50_ms": p50, "p99_ms": p99,
             "ms_per_step": 1000.0 * total_s / args.steps,
-            "product_edges_per_s": sum(r[1]["product_edges"] for r in m["recs"]) / total_s,
+            "product_edges_per_s": sum(r[0]["product_edges"] for r in m["recs"]) / total_s,
             "roofline": {"achieved": ach, "frac": ach / peak, "unit": "GB/s",
                          "avg_launch_ms": launch_s * 1000.0,
                          "achieved_push_bytes_only": push / len(m["recs"]) / launch_s / 1e9},
@@ -945,10 +969,10 @@ def main():
     if ws > 1:
         total_s = max_over_ranks(total_s, dist, "cuda")
     value = ws * nq * args.steps / total_s
-    p50, p99 = latency_summary(recs)
-    kern_ms = [r[1]["device_ms"] for r in recs]
+    p50, p99 = latency_summary(m["lat"])
+    kern_ms = [r[0]["device_ms"] for r in recs]
     push_bytes, sweep_bytes = algorithmic_bytes(recs, W_words)
-    prod_edges = sum(r[1]["product_edges"] for r in recs)
+    prod_edges = sum(r[0]["product_edges"] for r in recs)
     alg_bytes_per_launch = (push_bytes + sweep_bytes) / len(recs)
     avg_launch_s = sum(kern_ms) / len(kern_ms) / 1000.0
     achieved = alg_bytes_per_launch / avg_launch_s / 1e9

@@ -405,6 +405,36 @@ def rpq_query(g: Graph, nfa: Nfa, source: int, max_levels: int = 0, out=None, st
     return (res, st.as_dict()) if with_stats else res
 
 
+class QueryRunner:
+    """Repeated single-source queries into one device tensor ``out`` on one
+    stream: the ctypes arguments that do not change between calls are built
+    once, so a call costs the library's own work and one foreign call.
+    ``run(nfa, source)`` returns the answer count; with ``with_stats`` the
+    statistics of the last call are in ``self.stats`` (an :class:`RpqStats`,
+    overwritten by the next call)."""
+
+    def __init__(self, g: Graph, out, stream=None, max_levels: int = 0,
+                 with_stats: bool = False):
+        self._g, self._out = g, out  # kept alive while the runner is
+        self._f = lib().rpq_query
+        self._gh = g.h
+        self._optr = _ptr(out)
+        self._cap = ctypes.c_int64(out.numel())
+        self._levels = ctypes.c_int32(int(max_levels))
+        self._cnt = ctypes.c_int64()
+        self._pcnt = ctypes.byref(self._cnt)
+        self.stats = RpqStats() if with_stats else None
+        self._pst = ctypes.byref(self.stats) if with_stats else None
+        self._sh = _stream_handle(stream)
+
+    def run(self, nfa: Nfa, source: int) -> int:
+        st = self._f(self._gh, nfa.h, source, self._levels, self._optr, self._cap, self._pcnt,
+                     self._pst, self._sh)
+        if st != RPQ_OK:
+            _check(st)
+        return self._cnt.value
+
+
 def _answer_call(call, out, with_stats):
     """Shared marshalling of the calls that return one answer like rpq_query:
     ``call(out_ptr, capacity, count_ref, stats_ref)``."""

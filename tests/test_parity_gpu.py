@@ -213,6 +213,32 @@ def test_device_and_bitset_outputs():
     assert (dbits.cpu().numpy().view(np.uint64) == bits).all()
 
 
+def test_query_runner_matches_oracle():
+    """The prepared call (the bench's timed loop) gives the oracle's answers,
+    and its statistics equal those of a plain rpq_query call."""
+    import torch
+
+    w = W.config2(per_template=3)
+    g = w.graph
+    gg = load(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    lean = R.QueryRunner(gg, out)
+    full = R.QueryRunner(gg, out, with_stats=True)
+    og = O.OracleGraph(g.n, g.n_labels, g.src, g.dst, g.lab)
+    for q in w.queries:
+        nfa = R.rpq_nfa_compile(q.regex, g.n_labels)
+        exp = og.ssr(oracle_compile(q.regex, g.n_labels), q.source)["answer"]
+        cnt = lean.run(nfa, q.source)
+        assert out[:cnt].cpu().numpy().tolist() == exp.tolist(), q
+        assert full.run(nfa, q.source) == cnt
+        _, st = R.rpq_query(gg, nfa, q.source, out=out, with_stats=True)
+        for k in ("levels", "visited_pairs", "expanded_pairs", "product_edges", "push_bytes",
+                  "answer_count"):
+            assert getattr(full.stats, k) == st[k], (k, q)
+    with pytest.raises(R.RpqError):
+        lean.run(R.rpq_nfa_compile("0", g.n_labels), g.n)
+
+
 # ------------------------------------------------------ small workload ---
 
 def test_config1_golden():
