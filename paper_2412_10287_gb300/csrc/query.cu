@@ -44,6 +44,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <unistd.h>  // environ
 
 #include "graph.h"
 
@@ -217,14 +218,23 @@ struct KParams {
     alignas(16) uint8_t tab[kInlineTables];
 };
 
-constexpr int kTraceFields = 12;  // t_plan, t_expand, t_barrier, pairs, push units, pull units,
+constexpr int kTraceFields = 16;  // t_plan, t_expand, t_barrier, pairs, push units, pull units,
                                   // grid, push bytes of the level's rows, block 0's chunks done,
-                                  // its short rows done, ~(first CTA done), last CTA done
+                                  // its short rows done, ~(first CTA done), last CTA done, and on
+                                  // grid levels: last CTA whose warps all ended the expansion,
+                                  // last CTA done measuring its buffer, block 0 past the barrier,
+                                  // block 0 done sorting the level (overflow only)
 constexpr int kTraceLevels = 4096;
 
 __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsigned long long v) {
     if (p.trace && blockIdx.x == 0 && threadIdx.x == 0 && j < p.trace_cap)
         p.trace[(size_t)j * kTraceFields + f] = v;
+}
+
+// The latest of every CTA's time for field f (thread 0 of each CTA).
+__device__ __forceinline__ void trace_last(const KParams &p, int j, int f) {
+    if (p.trace && threadIdx.x == 0 && j < p.trace_cap)
+        atomicMax(&p.trace[(size_t)j * kTraceFields + f], global_timer_ns());
 }
 
 // ------------------------------------------------------------ barrier ----
@@ -2184,10 +2194,16 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             // every CTA measures what it discovered, from its buffer; if a
             // buffer overflowed, the grid measures the level again from the
             // lists
+            if (p.trace) {
+                __syncthreads();
+                trace_last(p, j, 12);
+            }
             flush_discoveries(p, sh, sh.cv[0], (j + 1) % 3);
             const bool fits = measure_buffer(p, sh, sh.cv[0], (j + 1) % 3, s_acc);
+            trace_last(p, j, 13);
             const int r = grid_sync(p, !fits);
             if (r < 0) return;
+            trace_put(p, j, 14, global_timer_ns());
             if (r > 0) {
                 if (lead) measure_reset(p, sh, (j + 1) % 3);
                 if (!grid_barrier(p)) return;
@@ -2197,6 +2213,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
                 // no flags
                 if (lead && threadIdx.x == 0) atomicAnd(&p.c->gen_status, ~kOverflowBits);
                 if (!sort_level(p, sh, j)) return;
+                trace_put(p, j, 15, global_timer_ns());
                 measure_level(p, sh, sh.cv[0], (j + 1) % 3, (int)blockIdx.x, (int)gridDim.x,
                               s_acc);
                 if (!grid_barrier(p)) return;
@@ -2605,11 +2622,40 @@ struct Tables {
     std::vector<QUnit> units;
     std::vector<int32_t> t_unit, t_state, u_group;
     long long row_need = 0, chunk_need = 0, srow_need = 0;
+    void clear() {
+        groups.clear();
+        units.clear();
+        t_unit.clear();
+        t_state.clear();
+        u_group.clear();
+        row_need = chunk_need = srow_need = 0;
+    }
 };
 
+// A (key, mask) list sorted by key with the masks of equal keys OR-ed.
+struct KeyMask {
+    int64_t key;
+    uint64_t mask;
+};
+void merge_keys(std::vector<KeyMask> &v) {
+    std::sort(v.begin(), v.end(), [](const KeyMask &x, const KeyMask &y) { return x.key < y.key; });
+    size_t o = 0;
+    for (size_t i = 0; i < v.size(); i++) {
+        if (o > 0 && v[o - 1].key == v[i].key) v[o - 1].mask |= v[i].mask;
+        else v[o++] = v[i];
+    }
+    v.resize(o);
+}
+
+// t must be empty (Tables::clear).  Allocation-free once this thread's
+// scratch lists and t have grown to the automaton's size.
 rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
-    // group (q, d) -> targets; unit (d, q') -> sources
-    std::map<std::pair<int, int>, uint64_t> gmap, umap;
+    // group (q, d) -> targets, ordered by q then d; unit (d, q') -> sources,
+    // ordered by d then q'
+    thread_local std::vector<KeyMask> gk, uk;
+    gk.clear();
+    uk.clear();
+    const int64_t D = 2 * (int64_t)g->L;
     for (size_t i = 0; i < a.from.size(); i++) {
         const int s = a.sym[i];
         const int lab = s < a.L ? s : s - a.L;
@@ -2618,35 +2664,41 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
             return fail(RPQ_ERR_INVALID, "automaton label %d is not a label of the graph (L=%d)",
                         lab, g->L);
         const int d = inv ? g->L + lab : lab;
-        gmap[{a.from[i], d}] |= 1ull << a.to[i];
-        umap[{d, a.to[i]}] |= 1ull << a.from[i];
+        gk.push_back({(int64_t)a.from[i] * D + d, 1ull << a.to[i]});
+        uk.push_back({(int64_t)d * kMaxStates + a.to[i], 1ull << a.from[i]});
     }
-    if ((int)gmap.size() > kMaxGroups || (int)umap.size() > kMaxUnits)
+    merge_keys(gk);
+    merge_keys(uk);
+    if ((int)gk.size() > kMaxGroups || (int)uk.size() > kMaxUnits)
         return fail(RPQ_ERR_INVALID, "automaton has too many (state, label) pairs");
-    std::map<std::pair<int, int>, int> uidx;
-    for (auto &kv : umap) {
+    for (const KeyMask &km : uk) {
         QUnit u{};
-        u.d = kv.first.first;
-        u.q2 = kv.first.second;
-        u.smask = kv.second;
+        u.d = (int32_t)(km.key / kMaxStates);
+        u.q2 = (int32_t)(km.key % kMaxStates);
+        u.smask = km.mask;
         u.in_dir = g->inverse_dir(u.d);
         const DevAdj &A = g->adj[u.in_dir];
         u.in_rows = A.fmt == ADJ_EMPTY ? 0 : A.nrows;
         u.in_nnz = A.nnz;
-        uidx[kv.first] = (int)t->units.size();
         t->units.push_back(u);
     }
-    for (auto &kv : gmap) {
+    auto unit_of = [&](int d, int q2) {
+        const int64_t key = (int64_t)d * kMaxStates + q2;
+        const auto it = std::lower_bound(uk.begin(), uk.end(), key,
+                                         [](const KeyMask &x, int64_t k) { return x.key < k; });
+        return (int32_t)(it - uk.begin());
+    };
+    for (const KeyMask &km : gk) {
         QGroup G{};
-        G.q = kv.first.first;
-        G.d = kv.first.second;
-        G.tmask = kv.second;
+        G.q = (int32_t)(km.key / D);
+        G.d = (int32_t)(km.key % D);
+        G.tmask = km.mask;
         G.t_first = (int32_t)t->t_unit.size();
         uint64_t m = G.tmask;
         while (m) {
             const int q2 = __builtin_ctzll(m);
             m &= m - 1;
-            t->t_unit.push_back(uidx[{G.d, q2}]);
+            t->t_unit.push_back(unit_of(G.d, q2));
             t->t_state.push_back(q2);
         }
         G.t_count = (int32_t)t->t_unit.size() - G.t_first;
@@ -2682,8 +2734,11 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
 // block 0's timestamps (ns, relative to the kernel start) with the frontier
 // size, the number of push / pull units, whether the level ran on the
 // whole grid (1) or on CTA 0 alone (0), the push-model bytes of its rows,
-// block 0's end of the long-row and short-row phases, and the first and last
-// CTA's end of the level.
+// block 0's end of the long-row and short-row phases, the first and last
+// CTA's end of the expansion (thread 0), and on grid levels the last CTA
+// whose warps all ended the expansion, the last CTA done measuring its
+// discovery buffer, block 0 past the barrier that follows, and block 0 done
+// sorting the level (levels re-measured from the lists only).
 void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int levels,
                  cudaStream_t st) {
     std::vector<unsigned long long> h((size_t)kTraceFields * levels), gs(kTraceFields);
@@ -2704,9 +2759,12 @@ void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int le
     for (int j = 0; j < levels; j++) {
         const unsigned long long *r = &h[(size_t)j * kTraceFields];
         if (r[0] == 0) break;
-        fprintf(f, "%s[%lld, %lld, %lld, %llu, %llu, %llu, %llu, %llu, %lld, %lld, %lld, %lld]",
+        fprintf(f,
+                "%s[%lld, %lld, %lld, %llu, %llu, %llu, %llu, %llu, %lld, %lld, %lld, %lld, %lld, "
+                "%lld, %lld, %lld]",
                 j ? ", " : "", rel(r[0]), rel(r[1]), rel(r[2]), r[3], r[4], r[5], r[6], r[7],
-                rel(r[8]), rel(r[9]), rel(r[10] ? ~r[10] : 0), rel(r[11]));
+                rel(r[8]), rel(r[9]), rel(r[10] ? ~r[10] : 0), rel(r[11]), rel(r[12]), rel(r[13]),
+                rel(r[14]), rel(r[15]));
     }
     fprintf(f, "]}\n");
     fclose(f);
@@ -2760,9 +2818,27 @@ rpq_status place_tables(const Tables &t, KParams &p, uint8_t *staging, uint8_t *
     return RPQ_OK;
 }
 
+// The RPQ_ variables of the environment (tuning overrides), taken by one
+// pass over it at the start of each launch's set-up instead of one lookup
+// per setting; env_float reads the taking of its own thread.
+struct EnvSnapshot {
+    int n = 0;
+    const char *kv[64];
+};
+thread_local EnvSnapshot tl_env;
+
+void env_snapshot() {
+    tl_env.n = 0;
+    for (char **e = environ; e && *e && tl_env.n < 64; e++)
+        if (strncmp(*e, "RPQ_", 4) == 0) tl_env.kv[tl_env.n++] = *e;
+}
+
 float env_float(const char *name, float dflt) {
-    const char *v = getenv(name);
-    return v ? (float)atof(v) : dflt;
+    const size_t len = strlen(name);
+    for (int i = 0; i < tl_env.n; i++)
+        if (strncmp(tl_env.kv[i], name, len) == 0 && tl_env.kv[i][len] == '=')
+            return (float)atof(tl_env.kv[i] + len + 1);
+    return dflt;
 }
 
 // Big levels on big graphs: when the row offsets of a label no longer fit
@@ -2925,7 +3001,9 @@ rpq_status run_query_ex(rpq_graph *g, const Automaton &a, QueryExtras *x, int32_
         return fail(RPQ_ERR_INVALID, "first-reach levels need the answer in device memory");
     if (max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
     if (a.S <= 0 || a.S > kMaxStates) return fail(RPQ_ERR_INVALID, "automaton has %d states", a.S);
-    Tables t;
+    env_snapshot();
+    thread_local Tables t;  // reused: no host allocation once grown
+    t.clear();
     rpq_status s = build_tables(g, a, &t);
     if (s != RPQ_OK) return s;
     std::unique_ptr<QueryWorkspace> ws =
@@ -3283,7 +3361,9 @@ extern "C" rpq_status rpq_query_noalloc(const rpq_graph *g, const rpq_nfa *nfa, 
     RPQ_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != g->device)
         return fail(RPQ_ERR_INVALID, "make the graph's device (%d) current first", g->device);
-    Tables t;
+    env_snapshot();
+    thread_local Tables t;  // reused: no host allocation once grown
+    t.clear();
     rpq_status s = build_tables(g, a, &t);
     if (s != RPQ_OK) return s;
 

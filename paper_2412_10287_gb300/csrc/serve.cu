@@ -99,9 +99,10 @@ struct rpq_server {
     // failure (back-off) and raised again as queries complete
     int slot_cap = 0;
     int64_t oom_retries = 0;
-    // engine 0: grid share divisor of a query that finds the queue empty (2:
-    // at 2,000 q/s on rmat20 half the grid gave p50 0.17 ms and p99 1.2 ms,
-    // the whole grid 0.39 / 1.3 ms, a quarter 0.08 / 1.7 ms)
+    // engine 0: a query is launched on 1 / d of the grid, d = the queries in
+    // flight (itself included) plus those still queued, and at least
+    // idle_div (2: at 2,000 q/s on rmat20 half the grid for a lone query
+    // gave p50 0.14 ms and p99 1.26 ms, the whole grid 0.28 / 1.37 ms)
     int idle_div = 2;
     // statistics
     int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, level_steps = 0;
@@ -426,7 +427,8 @@ void slot_worker_main(rpq_server *s) {
             s->queue.pop_front();
             need = query_bytes(s, q.a);
             admit_account(s, need);
-            grid_div = std::min(s->lanes_max, std::max(s->idle_div, 1 + (int)s->queue.size()));
+            grid_div = std::min(s->lanes_max,
+                                std::max(s->idle_div, s->inflight_n + (int)s->queue.size()));
         }
         int64_t cnt = 0;
         rpq_stats qs{};
