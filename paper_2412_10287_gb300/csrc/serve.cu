@@ -415,6 +415,8 @@ void slot_worker_main(rpq_server *s) {
         Pending q;
         int64_t need = 0;
         int grid_div = s->lanes_max;
+        int alone_at_admit = 0;              // no other query in flight when admitted
+        int64_t completed_at_admit = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] {
@@ -427,6 +429,8 @@ void slot_worker_main(rpq_server *s) {
             s->queue.pop_front();
             need = query_bytes(s, q.a);
             admit_account(s, need);
+            alone_at_admit = s->inflight_n == 1;
+            completed_at_admit = s->completed;
             grid_div = std::min(s->lanes_max,
                                 std::max(s->idle_div, s->inflight_n + (int)s->queue.size()));
         }
@@ -439,7 +443,11 @@ void slot_worker_main(rpq_server *s) {
         if (r == RPQ_OK) ans.assign(buf.begin(), buf.begin() + cnt);
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            if (r == RPQ_ERR_OOM && s->inflight_n > 1) {
+            // another query held device memory during this attempt if one was
+            // in flight when it was admitted, still is, or ended meanwhile
+            const bool shared =
+                !alone_at_admit || s->inflight_n > 1 || s->completed != completed_at_admit;
+            if (r == RPQ_ERR_OOM && shared) {
                 // device memory ran out beside the other queries in flight:
                 // admit fewer at once and run this query again when one ends
                 retire_account(s, need);

@@ -178,19 +178,24 @@ def _ptr(x):
 
 _ALLOC_CB = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+# Every callback pair ever installed stays referenced until exit: memory a
+# pair allocated goes back through that pair's free callback, possibly after
+# another allocator has been installed (a graph loaded under the first one
+# and freed later).
 _alloc_refs = []
 
 
 def rpq_set_allocator(alloc=None, free=None):
     """Install Python callables (size -> int pointer, pointer -> None) as the
-    device allocator, or restore cudaMalloc with no arguments."""
+    device allocator, or restore cudaMalloc with no arguments.  Buffers
+    allocated before the change are still freed through the callable that
+    allocated them, so that callable must keep working until they are."""
     if alloc is None:
         _check(lib().rpq_set_allocator(None, None, None))
-        _alloc_refs.clear()
         return
     a = _ALLOC_CB(lambda size, ctx: int(alloc(int(size)) or 0))
     f = _FREE_CB(lambda ptr, ctx: free(int(ptr)))
-    _alloc_refs[:] = [a, f]
+    _alloc_refs.append((a, f))
     _check(lib().rpq_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p),
                                    None))
 

@@ -146,5 +146,5 @@ def test_server_backs_off_after_allocation_failures(capped):
         assert capped.refused > 0 and st["oom_retries"] > 0
     finally:
         srv.close()
-    gg.close()
-    og.close()
+        gg.close()  # its memory goes back through the capped allocator
+        og.close()
