@@ -231,6 +231,14 @@ __device__ __forceinline__ void trace_put(const KParams &p, int j, int f, unsign
         p.trace[(size_t)j * kTraceFields + f] = v;
 }
 
+// Field f of the launch's own trace row (block 0, thread 0): 0 start, 1
+// level 0 measured, 2 loop end, 3 end; 4 tables loaded, 5 seeds set, 6
+// level 0 advanced, 7 level 0 planned.
+__device__ __forceinline__ void trace_launch(const KParams &p, int f) {
+    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0)
+        p.trace[(size_t)(p.trace_cap) * kTraceFields + f] = global_timer_ns();
+}
+
 // The latest of every CTA's time for field f (thread 0 of each CTA).
 __device__ __forceinline__ void trace_last(const KParams &p, int j, int f) {
     if (p.trace && threadIdx.x == 0 && j < p.trace_cap)
@@ -2037,8 +2045,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
     __shared__ long long s_claim;
     __shared__ unsigned long long s_acc[2];
     const bool lead = blockIdx.x == 0;
-    if (p.trace && lead && threadIdx.x == 0)
-        p.trace[(size_t)(p.trace_cap) * kTraceFields + 0] = global_timer_ns();
+    trace_launch(p, 0);
     // the layout's pointers live in shared memory, not in 30 registers
     __shared__ Shared s_layout;
     if (threadIdx.x == 0) s_layout = carve(p, smem);
@@ -2056,6 +2063,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
     if (threadIdx.x < 2) s_acc[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_nd = 0;
     __syncthreads();
+    trace_launch(p, 4);
     if (p.clear_first) {
         const size_t words = (size_t)p.S * p.W;
         for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < words;
@@ -2114,14 +2122,16 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
                 }
             }
         }
+        trace_launch(p, 5);
         flush_discoveries(p, sh, sh.cv[1], 0);
         if (!measure_buffer(p, sh, sh.cv[1], 0, s_acc))
             measure_level(p, sh, sh.cv[1], 0, 0, 1, s_acc);
         __syncthreads();
-        if (p.trace && threadIdx.x == 0)
-            p.trace[(size_t)(p.trace_cap) * kTraceFields + 1] = global_timer_ns();
+        trace_launch(p, 1);
         level_advance(p, 0, sh, true, true);
+        trace_launch(p, 6);
         plan = level_plan(p, 0, sh, true);
+        trace_launch(p, 7);
     }
     bool cur_smem = lead;  // level j's counters are in CTA 0's shared memory
     bool prev_grid = false;  // level j-1 ran on the grid (its frontier bits exist)
@@ -2252,8 +2262,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
         level_advance(p, j, sh, lead, cur_smem);
         plan = level_plan(p, j, sh, lead);
     }
-    if (p.trace && lead && threadIdx.x == 0)
-        p.trace[(size_t)(p.trace_cap) * kTraceFields + 2] = global_timer_ns();
+    trace_launch(p, 2);
     // frontier bits exist only when the last levels ran on the grid
     const bool f_live = grid && !from_gate_final;
     bool solo_end = false;
@@ -2281,8 +2290,7 @@ __global__ void __launch_bounds__(kThreads, 3) rpq_query_kernel(const __grid_con
             p.c->vcount[q] = sh.vstart[q] + (long long)sh.fl[q];
         write_result(p, sh, solo_end);
     }
-    if (p.trace && lead && threadIdx.x == 0)
-        p.trace[(size_t)(p.trace_cap) * kTraceFields + 3] = global_timer_ns();
+    trace_launch(p, 3);
 }
 
 // ------------------------------------------------- path outputs (kernels) --
@@ -2730,7 +2738,9 @@ rpq_status build_tables(const rpq_graph *g, const Automaton &a, Tables *t) {
     return RPQ_OK;
 }
 
-// Appends one JSON line per query: the kernel's phase times and, per level,
+// Appends one JSON line per query: the kernel's phase times (`kernel`, and
+// within the prologue `prologue`: tables loaded, seeds set, level 0 advanced
+// and planned) and, per level,
 // block 0's timestamps (ns, relative to the kernel start) with the frontier
 // size, the number of push / pull units, whether the level ran on the
 // whole grid (1) or on CTA 0 alone (0), the push-model bytes of its rows,
@@ -2754,8 +2764,11 @@ void write_trace(const char *path, QueryWorkspace *ws, int S, int source, int le
     FILE *f = fopen(path, "a");
     if (!f) return;
     auto rel = [&](unsigned long long t) { return t && gs[0] ? (long long)(t - gs[0]) : -1LL; };
-    fprintf(f, "{\"source\": %d, \"states\": %d, \"kernel\": [%lld, %lld, %lld, %lld], \"levels\": [",
-            source, S, rel(gs[0]), rel(gs[1]), rel(gs[2]), rel(gs[3]));
+    fprintf(f,
+            "{\"source\": %d, \"states\": %d, \"kernel\": [%lld, %lld, %lld, %lld], "
+            "\"prologue\": [%lld, %lld, %lld, %lld], \"levels\": [",
+            source, S, rel(gs[0]), rel(gs[1]), rel(gs[2]), rel(gs[3]), rel(gs[4]), rel(gs[5]),
+            rel(gs[6]), rel(gs[7]));
     for (int j = 0; j < levels; j++) {
         const unsigned long long *r = &h[(size_t)j * kTraceFields];
         if (r[0] == 0) break;
