@@ -565,7 +565,7 @@ def run_serve(args, R, torch, g=None, gg=None):
         if q.regex not in nfas:
             nfas[q.regex] = R.rpq_nfa_compile(q.regex, g.n_labels)
     qs = w.queries
-    engines = {"slots": dict(max_lanes=12, engine=0), "lanes": dict(max_lanes=256, max_states=16,
+    engines = {"slots": dict(max_lanes=8, engine=0), "lanes": dict(max_lanes=256, max_states=16,
                                                                     engine=1)}
     for cfg in engines.values():  # warm-up burst
         srv = R.Server(gg, **cfg)
@@ -632,7 +632,7 @@ def run_serve(args, R, torch, g=None, gg=None):
     sat_seq = sat_n / (time.perf_counter() - t0)
     return {"workload": f"rmat20_serve: Poisson arrivals at 2,000 q/s for "
                         f"{args.serve_seconds + 1.0:.0f} s ({len(qs)} queries, mixed templates "
-                        "of 1-12 DFA states); server engine 0 = 12 concurrent query slots "
+                        "of 1-12 DFA states); server engine 0 = 8 concurrent query slots "
                         "(queries_per_s), engine 1 = 256 bit lanes",
             "queries_per_s": st_srv["qps"], "p50_ms": st_srv["p50_ms"],
             "p99_ms": st_srv["p99_ms"], "gpu_launches": st_srv["gpu_launches"],

@@ -99,10 +99,11 @@ struct rpq_server {
     // failure (back-off) and raised again as queries complete
     int slot_cap = 0;
     int64_t oom_retries = 0;
-    // engine 0: a query is launched on 1 / d of the grid, d = the queries in
-    // flight (itself included) plus those still queued, and at least
-    // idle_div (2: at 2,000 q/s on rmat20 half the grid for a lone query
-    // gave p50 0.14 ms and p99 1.26 ms, the whole grid 0.28 / 1.37 ms)
+    // engine 0: a query is launched on 1 / d of the grid, d = 1 + the queries
+    // still queued when it is admitted, and at least idle_div (2: at 2,000
+    // q/s on rmat20 half the grid for a query that finds the queue empty gave
+    // p50 0.16 ms and p99 1.16 ms, the whole grid 0.37 / 1.28 ms; counting
+    // the queries in flight into d as well gave 0.13 / 1.23 ms)
     int idle_div = 2;
     // statistics
     int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, level_steps = 0;
@@ -402,6 +403,11 @@ void worker_main(rpq_server *s) {
 // half the grid (RPQ_SERVE_IDLE_DIV), so that one arriving meanwhile finds
 // room beside it.  (A query admitted while others fill the grid waits for
 // room either way: a cooperative launch starts only when all its CTAs fit.)
+// Query slots of a server on engine 0 by default: at 2,000 q/s on rmat20, 4,
+// 6, 8 and 12 slots gave the same latencies (p50 0.15-0.16 ms, p99 1.16-1.17
+// ms) and 9.7K, 11.5K, 12.7K and 11.1K q/s at saturation.
+constexpr int kServeSlots = 8;
+
 void slot_worker_main(rpq_server *s) {
     cudaSetDevice(s->g->device);
     cudaStream_t st = nullptr;
@@ -431,8 +437,7 @@ void slot_worker_main(rpq_server *s) {
             admit_account(s, need);
             alone_at_admit = s->inflight_n == 1;
             completed_at_admit = s->completed;
-            grid_div = std::min(s->lanes_max,
-                                std::max(s->idle_div, s->inflight_n + (int)s->queue.size()));
+            grid_div = std::min(s->lanes_max, std::max(s->idle_div, 1 + (int)s->queue.size()));
         }
         int64_t cnt = 0;
         rpq_stats qs{};
@@ -487,7 +492,7 @@ extern "C" rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_confi
     if (cfg) c = *cfg;
     if (c.engine != 0 && c.engine != 1) return fail(RPQ_ERR_INVALID, "engine must be 0 or 1");
     if (c.engine == 0) {
-        const int slots = c.max_lanes ? c.max_lanes : kDefaultSlots;
+        const int slots = c.max_lanes ? c.max_lanes : kServeSlots;
         if (slots <= 0 || slots > 64) return fail(RPQ_ERR_INVALID, "max_lanes (slots) must be in [1, 64]");
         if (c.max_levels < 0) return fail(RPQ_ERR_INVALID, "max_levels must be >= 0");
         std::unique_ptr<rpq_server> s(new rpq_server());
