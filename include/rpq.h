@@ -361,7 +361,7 @@ rpq_status rpq_query_batch(const rpq_graph *g, int32_t n, const rpq_nfa *const *
 
 typedef struct rpq_serve_config {
     int32_t max_lanes;       /* queries in flight on the device: query slots for engine 0
-                                (0 = 12, at most 64), bit lanes for engine 1 (0 = 256) */
+                                (0 = 8, at most 64), bit lanes for engine 1 (0 = 256) */
     int32_t max_states;      /* state slots per lane, engine 1 (0 = 16) */
     int32_t queue_capacity;  /* submitted-but-not-admitted queries (0 = 65536) */
     int64_t memory_budget;   /* bytes of device state the admitted queries may hold at once
@@ -409,10 +409,11 @@ typedef struct rpq_serve_stats {
  * admission: a query that finds k - 1 others waiting runs on 1/k of the grid
  * (at most 1/max_lanes), one that finds the queue empty on half of it
  * (RPQ_SERVE_IDLE_DIV changes that divisor).  When a
- * query's device allocation fails while other queries are in flight, engine
- * 0 puts it back at the head of the queue and admits fewer queries at once
- * (raised again as queries complete); a query that fails alone completes
- * with RPQ_ERR_OOM. */
+ * query's device allocation fails while other queries held memory during its
+ * attempt (in flight when it was admitted, still, or finished meanwhile),
+ * engine 0 puts it back at the head of the queue and admits fewer queries at
+ * once (raised again as queries complete); a query that fails alone
+ * completes with RPQ_ERR_OOM. */
 rpq_status rpq_serve_create(const rpq_graph *g, const rpq_serve_config *cfg, rpq_server **out);
 
 /* Non-blocking.  RPQ_ERR_BUSY when the queue is full.  The automaton must
