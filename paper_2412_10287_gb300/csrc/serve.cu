@@ -416,7 +416,6 @@ void slot_worker_main(rpq_server *s) {
         s->fatal = RPQ_ERR_CUDA;
         return;
     }
-    std::vector<int32_t> buf((size_t)s->g->n);
     for (;;) {
         Pending q;
         int64_t need = 0;
@@ -441,11 +440,17 @@ void slot_worker_main(rpq_server *s) {
         }
         int64_t cnt = 0;
         rpq_stats qs{};
-        const rpq_status r = run_query_slot(s->g, q.a, q.source, s->max_levels, nullptr,
-                                            (int64_t)buf.size(), nullptr, buf.data(), &qs, &cnt,
-                                            st, grid_div);
+        // the answer stays in this thread's pinned host buffer (the kernel
+        // writes small ones there directly) and is copied once, into the
+        // ticket's result
+        const rpq_status r = run_query_slot(s->g, q.a, q.source, s->max_levels, nullptr, 0,
+                                            nullptr, nullptr, &qs, &cnt, st, grid_div, true);
         std::vector<int32_t> ans;
-        if (r == RPQ_OK) ans.assign(buf.begin(), buf.begin() + cnt);
+        if (r == RPQ_OK && cnt > 0) {
+            const int32_t *h = nullptr;
+            int64_t hc = 0;
+            if (last_host_answer(&h, &hc) == RPQ_OK) ans.assign(h, h + hc);
+        }
         {
             std::lock_guard<std::mutex> lk(s->mu);
             // another query held device memory during this attempt if one was
