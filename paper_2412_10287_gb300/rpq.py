@@ -625,7 +625,10 @@ class Server:
                 return None
             if s == RPQ_OK:
                 self._nfas.pop(ticket, None)
-                return buf[: cnt.value].copy()
+                n = int(cnt.value)
+                # a small answer is copied out of the 64K-entry buffer; a
+                # large one (the buffer was sized for it) is returned as is
+                return buf if n == cap else buf[:n].copy()
             cap = int(cnt.value)
 
     def drain(self, timeout_ms: int = 600000):
