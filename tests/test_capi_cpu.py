@@ -118,3 +118,22 @@ def test_too_many_states_rejected():
     # a chain of 70 labels has 71 states after minimisation
     with pytest.raises(R.RpqError):
         R.rpq_nfa_compile("/".join(["0"] * 70), 1)
+
+
+def test_answer_copy_small_and_threaded():
+    """The binding's copy of a host answer out of the library's buffer: the
+    plain copy below the threshold and the threaded one above it return the
+    same entries in fresh memory."""
+    import ctypes
+
+    import numpy as np
+
+    for n in (0, 1, 1000, R._PARALLEL_COPY_MIN - 1, R._PARALLEL_COPY_MIN,
+              3 * R._PARALLEL_COPY_MIN + 7):
+        src = np.arange(n, dtype=np.int32)[::-1].copy()
+        ptr = src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        got = R._copy_answer(ptr, n)
+        assert got.dtype == np.int32 and got.shape == (n,)
+        assert (got == src).all()
+        if n:
+            assert not np.shares_memory(got, src)
