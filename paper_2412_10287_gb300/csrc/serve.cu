@@ -393,6 +393,11 @@ void worker_main(rpq_server *s) {
     }
 }
 
+// Query slots of a server on engine 0 by default: at 2,000 q/s on rmat20, 4,
+// 6, 8 and 12 slots gave the same latencies (p50 0.15-0.16 ms, p99 1.16-1.17
+// ms) and 9.7K, 11.5K, 12.7K and 11.1K q/s at saturation.
+constexpr int kServeSlots = 8;
+
 // Engine 0: one admitted query at a time per worker, on its own stream.  A
 // query is admitted when a worker is free and its workspace fits the memory
 // budget beside those of the queries in flight (in arrival order: a query
@@ -403,11 +408,6 @@ void worker_main(rpq_server *s) {
 // half the grid (RPQ_SERVE_IDLE_DIV), so that one arriving meanwhile finds
 // room beside it.  (A query admitted while others fill the grid waits for
 // room either way: a cooperative launch starts only when all its CTAs fit.)
-// Query slots of a server on engine 0 by default: at 2,000 q/s on rmat20, 4,
-// 6, 8 and 12 slots gave the same latencies (p50 0.15-0.16 ms, p99 1.16-1.17
-// ms) and 9.7K, 11.5K, 12.7K and 11.1K q/s at saturation.
-constexpr int kServeSlots = 8;
-
 void slot_worker_main(rpq_server *s) {
     cudaSetDevice(s->g->device);
     cudaStream_t st = nullptr;
@@ -445,11 +445,13 @@ void slot_worker_main(rpq_server *s) {
         // ticket's result
         const rpq_status r = run_query_slot(s->g, q.a, q.source, s->max_levels, nullptr, 0,
                                             nullptr, nullptr, &qs, &cnt, st, grid_div, true);
+        rpq_status r_ans = r;
         std::vector<int32_t> ans;
         if (r == RPQ_OK && cnt > 0) {
             const int32_t *h = nullptr;
             int64_t hc = 0;
-            if (last_host_answer(&h, &hc) == RPQ_OK) ans.assign(h, h + hc);
+            if (last_host_answer(&h, &hc) == RPQ_OK && hc == cnt) ans.assign(h, h + hc);
+            else r_ans = RPQ_ERR_CUDA;  // the answer did not reach the host buffer
         }
         {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -468,7 +470,7 @@ void slot_worker_main(rpq_server *s) {
                 s->cv.notify_all();
                 continue;
             }
-            finish_ticket(s, q.ticket, r, std::move(ans), q.t_submit);
+            finish_ticket(s, q.ticket, r_ans, std::move(ans), q.t_submit);
             retire_account(s, need);
             if (r == RPQ_OK && s->slot_cap < s->lanes_max && s->completed % 16 == 0)
                 s->slot_cap++;
