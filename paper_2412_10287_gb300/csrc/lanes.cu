@@ -911,6 +911,8 @@ rpq_status lane_harvest(rpq_graph *g, LaneWorkspace *ws, const LParams &p,
 // Runs one lane group (<= 256 queries) to completion and writes the answers.
 // out (host or device per out_is_dev), capacity entries; offsets[i]
 // (group-relative) for i in [0, count].
+bool same_automaton(const Automaton &a, const Automaton &b);
+
 rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int32_t *sources,
                           int count, int32_t max_levels, int32_t *out, bool out_is_dev,
                           int64_t capacity, int64_t *offsets, int32_t *lane_levels, float *ms,
@@ -990,6 +992,16 @@ rpq_status lane_run_group(rpq_graph *g, const Automaton *const *autos, const int
     RPQ_CUDA_TRY(cudaMemsetAsync(ws->P.p, 0, words * 8, st));
     RPQ_CUDA_TRY(cudaMemsetAsync(ws->ctr.p, 0, sizeof(LaneCounters), st));
     LParams p = lane_params(g, ws.get(), o_dyn, o_dirs, o_units, o_srcs);
+    // pulling pays only when the lanes share one automaton: lanes of
+    // different automata are rarely all covered early, so a pulled scan
+    // rarely stops early (the mixed rmat20 batch: 1,083 q/s pulling at
+    // divisor 2 against 3,567 pushing).  RPQ_LANE_PULL_DIV still overrides.
+    if (!getenv("RPQ_LANE_PULL_DIV")) {
+        bool shared = true;
+        for (int i = 1; i < count && shared; i++)
+            shared = autos[i] == autos[0] || same_automaton(*autos[0], *autos[i]);
+        if (!shared) p.pull_div = 0;
+    }
     s = lane_seed(p, reinterpret_cast<const int32_t *>(dt + o_seed), (int)(seeds.size() / 5),
                   reinterpret_cast<const int32_t *>(dt + o_front), (int)frontier.size(), 0, st);
     if (s != RPQ_OK) return s;
